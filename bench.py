@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the 4-D spectral FNO block, forward + backward, on one GB300.
+
+One step = fno_block_fwd + fno_block_bwd (recompute of the forward spectrum
+inside the backward: per-block activation checkpointing) over one batch of the
+CO2-flow-like block workload: B=1, width 20, grid 128x128x128 (~2.1 M cells)
+x 32 time steps, kept modes 12/12/8/8, input a seeded anisotropic smooth
+Gaussian random field (correlation 20x20x4 cells, 8 steps), upstream gradient
+N(0, 1).  Metric: input points x channels processed per second (Gpoint*ch/s,
+B*C_in*Nx*Ny*Nz*Nt per step / step time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the baseline arm) on a bounded
+sample of the same workload (fewer channels), on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, correlation lengths)
+    "co2_block_128c_t32": (1, 20, 128, 128, 128, 32, 12, 12, 8, 8, (20.0, 20.0, 4.0, 8.0)),
+    "ns_block_64c_t16": (2, 20, 64, 64, 64, 16, 8, 8, 8, 6, (8.0, 8.0, 8.0, 8.0)),
+}
+DEFAULT_WORKLOAD = "co2_block_128c_t32"
+METRIC = "spectral block fwd+bwd Gpoint·ch/s & roofline %, BF16/split vs FP32 @ stated err"
+UNIT = "Gpoint*ch/s"
+CPU_SAMPLE_CHANNELS = 4
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return {"hbm_gbs": float(j["hbm_gbs"]), "bf16_tflops": float(j["bf16_tflops"]),
+                "sm_max_mhz": float(j.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic(name, d):
+    """Algorithmic (bytes, flops) of one launch of a kernel family for dims d (fwd+bwd step).
+
+    Bytes count each tensor the kernel must read or write once; flops count the
+    real multiply-adds of the separable pruned DFT GEMMs, the 1x1 linear and
+    the mixing (2 flops per multiply-add).
+    """
+    B, Ci, Co, Nx, Ny, Nz, Nt, Jx, Jy, Jz, Jt = (d[k] for k in (
+        "B", "Ci", "Co", "Nx", "Ny", "Nz", "Nt", "Jx", "Jy", "Jz", "Jt"))
+    Ng = Nx * Ny * Nz * Nt
+    C = Ci  # square blocks in the benchmark workloads
+    grid = 4 * B * C * Ng
+    t1 = 8 * B * C * Nx * Ny * Jz * Jt
+    ncolz = B * C * Nx * Ny
+    f_tz = ncolz * (Nz * Jt * Nt * 4 + Jz * Jt * Nz * 8)
+    f_inv = B * Nx * Ny * C * (Nz * Jt * Jz * 8 + Nz * Nt * Jt * 4)
+    f_lin = 2 * B * Ng * Ci * Co
+    if name.startswith("fno_fwd_tz"):
+        return grid + t1, f_tz
+    if name.startswith("fno_epi_fwd"):
+        return 2 * grid + t1, f_inv + f_lin
+    if name.startswith("fno_epi_da"):
+        return 4 * grid + t1, f_inv + 2 * f_lin
+    if name.startswith("fno_epi_dx"):
+        return 2 * grid + t1, f_inv + f_lin
+    return None, None
+
+
+def oracle_sample_time(wl_name, sample_channels, seed=1000):
+    """Seconds of one oracle fwd+bwd on the workload grid with fewer channels, and its units."""
+    import numpy as np
+
+    import oracle
+    from oracle import Dims
+    from paper_2211_12709_gb300 import inputs
+    B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[wl_name]
+    c = min(C, sample_channels)
+    d = Dims(1, c, c, Nx, Ny, Nz, Nt, mx, my, mz, mt)
+    x = inputs.normal((1, c) + d.grid, seed)
+    w = inputs.spectral_weights(c, c, d.modes, seed + 1)
+    wl, b = inputs.linear_params(c, c, seed + 2)
+    dz = inputs.normal((1, c) + d.grid, seed + 3)
+    pts = np.array([[0, 0, 0, 0]])
+    cores = oracle.threads()
+    t0 = time.perf_counter()
+    oracle.block_fwd(d, x, w, wl, b, full=False, pts=pts)
+    oracle.block_bwd(d, x, w, dz, wl, b, full=False, pts=pts)
+    dt = time.perf_counter() - t0
+    units = d.B * d.Ci * d.n_grid
+    return dt, units, cores, f"B=1, C_in=C_out={c} on the {Nx}x{Ny}x{Nz}x{Nt} grid, modes {mx}/{my}/{mz}/{mt}"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl_name = args.workload
+    B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[wl_name]
+    if args.warmup > 0:  # one untimed oracle pass stands for the warm-up steps
+        oracle_sample_time(wl_name, CPU_SAMPLE_CHANNELS)
+    times = []
+    units = cores = sample = None
+    for _ in range(args.steps):
+        dt, units, cores, sample = oracle_sample_time(wl_name, CPU_SAMPLE_CHANNELS)
+        times.append(dt)
+    tot = sum(times)
+    value = units * len(times) / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl_name, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2211_12709_gb300 import _lib, inputs, ops
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[args.workload]
+    modes = (mx, my, mz, mt)
+    Ng = Nx * Ny * Nz * Nt
+    cfg = 4 + rank  # independent replicas draw different seeds
+    # inputs in pinned host memory (the e2e leg copies them every step)
+    x_h = torch.from_numpy(inputs.grf((B, C), (Nx, Ny, Nz, Nt), ell, inputs.SEED_INPUT + cfg)).pin_memory()
+    dz_h = torch.from_numpy(inputs.normal((B, C, Nx, Ny, Nz, Nt), inputs.SEED_UPSTREAM + cfg)).pin_memory()
+    w = torch.from_numpy(inputs.spectral_weights(C, C, (2 * mx, 2 * my, 2 * mz, mt), inputs.SEED_SPECTRAL_W + cfg)).to(dev)
+    wl_np, b_np = inputs.linear_params(C, C, inputs.SEED_LINEAR + cfg)
+    wl, bias = torch.from_numpy(wl_np).to(dev), torch.from_numpy(b_np).to(dev)
+    x = x_h.to(dev)
+    dz = dz_h.to(dev)
+    z = torch.empty_like(x)
+    dx = torch.empty_like(x)
+    dw = torch.empty_like(w)
+    dwl = torch.empty_like(wl)
+    db = torch.empty_like(bias)
+    d = ops.dims_of(x, C, modes)
+    p = ops.precision_code(args.precision)
+    nws = max(_lib.fno_workspace_bytes(d, p, ops.OP_BLOCK_FWD), _lib.fno_workspace_bytes(d, p, ops.OP_BLOCK_BWD))
+    ws = torch.empty(nws, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = int(stream.cuda_stream)
+
+    def step():
+        _lib.fno_block_fwd(d, p, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                           z.data_ptr(), ws.data_ptr(), nws, sh)
+        _lib.fno_block_bwd(d, p, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                           dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(),
+                           db.data_ptr(), ws.data_ptr(), nws, sh)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    # ---- device-resident timed region ----
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    n0 = _lib.fno_launch_count()
+    _lib.fno_profile_start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    prof = _lib.fno_profile_stop()
+    launches = _lib.fno_launch_count() - n0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = B * C * Ng
+    value = units * world / (ms * 1e-3) / 1e9
+
+    # ---- end to end: pinned host inputs -> C ABI -> host results ----
+    e2e = None
+    if not args.no_e2e:
+        outs_h = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (z, dx, dw, dwl, db)]
+        h2d = (x_h.numel() + dz_h.numel()) * 4
+        d2h = sum(t.numel() * 4 for t in outs_h)
+        k2 = max(2, min(args.steps, 5))
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(k2):
+            x.copy_(x_h, non_blocking=True)
+            dz.copy_(dz_h, non_blocking=True)
+            step()
+            for hbuf, dbuf in zip(outs_h, (z, dx, dw, dwl, db)):
+                hbuf.copy_(dbuf, non_blocking=True)
+        e3.record(stream)
+        barrier()
+        ms2 = e2.elapsed_time(e3) / k2
+        if dist is not None:
+            t = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        e2e = {"value": units * world / (ms2 * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms2}
+
+    # ---- roofline of the dominant kernel ----
+    pk = peaks()
+    dd = {"B": B, "Ci": C, "Co": C, "Nx": Nx, "Ny": Ny, "Nz": Nz, "Nt": Nt,
+          "Jx": 2 * mx, "Jy": 2 * my, "Jz": 2 * mz, "Jt": mt}
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    kernel_share = {}
+    tot_prof = sum(v[1] for v in prof.values()) if prof else 0.0
+    for k, (n, t) in prof.items():
+        kernel_share[k] = {"launches": n, "ms": round(t, 4), "share": round(t / tot_prof, 4) if tot_prof else None}
+    if top is not None:
+        name, (n, t) = top
+        per_launch_ms = t / n
+        nbytes, nflops = algorithmic(name, dd)
+        if nbytes is not None:
+            gbs = nbytes / (per_launch_ms * 1e-3) / 1e9
+            tfl = nflops / (per_launch_ms * 1e-3) / 1e12
+            if args.precision == "fp32":
+                alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+                f_hbm, f_alu = gbs / pk["hbm_gbs"], tfl / alu_peak
+                if f_alu >= f_hbm:
+                    roof = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(alu_peak, 1),
+                            "unit": "TFLOP/s", "frac": round(f_alu, 4), "traffic": None,
+                            "kernel": name, "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock",
+                            "hbm_frac": round(f_hbm, 4)}
+                else:
+                    roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
+                            "unit": "GB/s", "frac": round(f_hbm, 4), "traffic": None,
+                            "kernel": name, "peak_src": pk["src"], "alu_frac": round(f_alu, 4)}
+            else:
+                roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
+                        "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 4), "traffic": None,
+                        "kernel": name, "peak_src": pk["src"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            dt, u, cores, sample = oracle_sample_time(args.workload, CPU_SAMPLE_CHANNELS)
+            cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32",
+                                           "bf16x3": "bf16x3+f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "B": B, "C_in": C, "C_out": C,
+                       "grid": [Nx, Ny, Nz, Nt], "modes": [mx, my, mz, mt], "precision": args.precision,
+                       "step": "fno_block_fwd + fno_block_bwd (backward recomputes the forward spectrum)",
+                       "l2": "inputs larger than L2 (5.4 GB per tensor); no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "kernels": kernel_share,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,142 @@
+/*
+ * fno.h -- C ABI of the GB300 (sm_103a) spectral FNO block library (libfno.so).
+ *
+ * The block is the FNO block of the paper's Alg. 2 (Sec. IV-C): a truncated
+ * real DFT of every channel onto the kept low modes (F then S), a complex
+ * per-mode channel mixing with learned weights (the einsum of Alg. 2), the
+ * zero-padded inverse DFT (S^T then F^T), and -- for the full block -- the
+ * pointwise 1x1 channel linear with bias of the original FNO that Sec. IV-C
+ * says the architecture follows, and the nonlinearity sigma of Alg. 1 (GELU,
+ * exact erf form):
+ *
+ *   theta_j(p) = 2 pi (kx x/Nx + ky y/Ny + kz z/Nz + kt t/Nt)
+ *   Xh[b,i,j]  = sum_p x[b,i,p] exp(-i theta_j(p))
+ *   Yh[b,o,j]  = sum_i Xh[b,i,j] w[i,o,j]
+ *   S[b,o,p]   = (1/N) sum_j c(kt_j) Re(Yh[b,o,j] exp(+i theta_j(p)))
+ *   spectral:  y = S
+ *   block:     z = GELU(S + sum_i x[b,i,p] w_lin[i,o] + bias[o])
+ *
+ * N = Nx Ny Nz Nt.  Kept modes: stored index jx < mx is frequency jx, jx >= mx
+ * is jx - 2 mx (same for y, z); t keeps kt = 0..mt-1 (real half spectrum).
+ * c(kt) = 1 at kt = 0 and at kt = Nt/2 (Nt even), 2 otherwise.
+ *
+ * Layouts (all C-contiguous, FP32, device memory):
+ *   x, dx            [B][C_in ][Nx][Ny][Nz][Nt]
+ *   y, z, dy, dz     [B][C_out][Nx][Ny][Nz][Nt]
+ *   w, dw            [C_in][C_out][2mx][2my][2mz][mt][2]   (re, im interleaved)
+ *   w_lin, dw_lin    [C_in][C_out]
+ *   bias, db         [C_out]
+ *
+ * Ownership: the caller owns every buffer, including the workspace whose size
+ * fno_workspace_bytes() returns; the library allocates no device memory.  The
+ * DFT basis tables are regenerated into the workspace (FP64 arithmetic on the
+ * device, stored in the precision the kernels read) on every call.
+ *
+ * Semantics: every call is asynchronous on the given stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream).  Gradients overwrite their
+ * outputs.  Inputs must not alias outputs.
+ *
+ * Errors: functions return an fno_status; nothing aborts or traps.  On any
+ * error other than FNO_ERR_CUDA nothing has been enqueued.  fno_last_error()
+ * returns a message for the calling thread's last failure.
+ */
+#ifndef FNO_GB300_FNO_H_
+#define FNO_GB300_FNO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Problem sizes.  B >= 0 (B = 0 is an empty batch); every other entry >= 1,
+ * 2 mx <= Nx, 2 my <= Ny, 2 mz <= Nz, mt <= Nt/2 + 1. */
+typedef struct fno_dims {
+  int64_t B, C_in, C_out, Nx, Ny, Nz, Nt, mx, my, mz, mt;
+} fno_dims;
+
+/* Arithmetic of the DFT contractions (accumulation is always FP32):
+ *   FNO_FP32    FP32 on the CUDA cores (the plain form)
+ *   FNO_TF32    TF32 tensor-core products
+ *   FNO_BF16    BF16 tensor-core products
+ *   FNO_BF16X3  split BF16 (hi + lo, three products) on the tensor cores   */
+typedef enum fno_precision {
+  FNO_FP32 = 0,
+  FNO_TF32 = 1,
+  FNO_BF16 = 2,
+  FNO_BF16X3 = 3
+} fno_precision;
+
+typedef enum fno_status {
+  FNO_OK = 0,
+  FNO_ERR_INVALID_ARG = -1, /* null required pointer, bad size, bad precision or op */
+  FNO_ERR_UNSUPPORTED = -2, /* valid sizes the kernels do not handle (message says which) */
+  FNO_ERR_WORKSPACE = -3,   /* workspace too small or misaligned (256-byte alignment) */
+  FNO_ERR_CUDA = -4,        /* a CUDA call failed; message carries its error string */
+  FNO_ERR_TIMEOUT = -5      /* a bounded device-side wait gave up */
+} fno_status;
+
+typedef enum fno_op {
+  FNO_OP_SPECTRAL_FWD = 0,
+  FNO_OP_SPECTRAL_BWD = 1,
+  FNO_OP_BLOCK_FWD = 2,
+  FNO_OP_BLOCK_BWD = 3
+} fno_op;
+
+/* Workspace bytes that op needs for these sizes and precision (0 on invalid
+ * arguments; see fno_last_error()). */
+size_t fno_workspace_bytes(const fno_dims* dims, int precision, int op);
+
+/* Spectral convolution forward, y = S(x; w)  (Alg. 2: F, S, einsum, S^T, F^T).
+ * x: input, w: complex weights, y: output; ws: workspace of ws_bytes. */
+int fno_spectral_fwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                     float* y, void* ws, size_t ws_bytes, void* stream);
+
+/* Spectral convolution backward for upstream gradient dy (Alg. 2 differentiated;
+ * the inverse is the adjoint of the forward operators, Sec. IV-C):
+ *   G   = (c(kt)/N) DFT(dy)
+ *   dw  = sum_b conj(Xh) G          (dL/dRe w, dL/dIm w), nullable
+ *   dx  = sum_j Re(sum_o conj(w) G exp(+i theta))   nullable
+ * At least one of dx, dw must be non-null. */
+int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                     const float* dy, float* dx, float* dw, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* Full FNO block forward: z = GELU(S(x; w) + w_lin^T x + bias). */
+int fno_block_fwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                  const float* w_lin, const float* bias, float* z, void* ws, size_t ws_bytes,
+                  void* stream);
+
+/* Full FNO block backward for upstream gradient dz.  The forward is recomputed
+ * from x (activation checkpointing: only the block input is kept between the
+ * passes).  dA = dz GELU'(A); db = sum dA; dw_lin = sum x dA^T; dw as in
+ * fno_spectral_bwd with G = (c(kt)/N) DFT(dA); dx = S^T-path + w_lin dA.
+ * All five outputs are required. */
+int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                  const float* w_lin, const float* bias, const float* dz, float* dx, float* dw,
+                  float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* fno_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int fno_version(void);
+
+/* Number of kernels this library has launched since it was loaded. */
+int64_t fno_launch_count(void);
+
+/* Optional per-kernel timing: while enabled, every launch is bracketed by CUDA
+ * events on its own stream.  fno_profile_stop() waits for the recorded events
+ * and aggregates them; fno_profile_entry() then reads kernel i's name, launch
+ * count and summed device time.  Host-side bookkeeping only; not thread safe. */
+int fno_profile_start(void);
+int fno_profile_stop(void);
+int fno_profile_count(void);
+int fno_profile_entry(int i, const char** name, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FNO_GB300_FNO_H_ */

@@ -1,0 +1,495 @@
+// fno_api.cu -- the C ABI of libfno: argument validation, workspace layout,
+// the stage sequence of each operation, error reporting and launch timing.
+//
+// Stage sequence of the forward block (Alg. 2, Sec. IV-C of the paper):
+//   tables -> fwd t,z (per column) -> fwd y -> fwd x -> mixing -> inv x -> inv y
+//   -> inv z,t + epilogue
+// The backward pass recomputes the forward spectrum from x (only the block
+// input is kept between the passes) and runs the adjoint chain: the forward
+// DFT kernels with the c(kt)/N-scaled t table produce G, the mixing adjoint
+// gives dW and the input-spectrum gradient, and the inverse kernels with the
+// unscaled t table bring it back to the grid.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fno_internal.h"
+
+namespace fno {
+
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  return fail(FNO_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ---- launch timing ----------------------------------------------------------
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct ProfAgg {
+  std::string name;
+  int64_t n;
+  double ms;
+};
+static std::mutex g_prof_mu;
+static bool g_prof = false;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+static size_t g_pool_used = 0;
+static std::vector<ProfAgg> g_agg;
+
+static cudaEvent_t pool_event() {
+  if (g_pool_used == g_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_pool.push_back(e);
+  }
+  return g_pool[g_pool_used++];
+}
+
+void prof_before(const char* name, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t a = pool_event(), b = pool_event();
+  if (!a || !b) return;
+  cudaEventRecord(a, s);
+  g_recs.push_back(ProfRec{name, a, b});
+}
+
+void prof_after(cudaStream_t s) {
+  if (!g_prof) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_recs.empty()) cudaEventRecord(g_recs.back().b, s);
+}
+
+int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// ---- validation and workspace layout ---------------------------------------
+static const int64_t kMaxChannels = 64;
+static const size_t kMaxSmem = 227 * 1024;
+
+static int to_dims(const fno_dims* dd, Dims* d) {
+  if (!dd) return fail(FNO_ERR_INVALID_ARG, "dims is NULL");
+  *d = Dims{dd->B, dd->C_in, dd->C_out, dd->Nx, dd->Ny, dd->Nz, dd->Nt,
+            dd->mx, dd->my, dd->mz, dd->mt, 0, 0, 0, 0, 0, 0};
+  if (d->B < 0) return fail(FNO_ERR_INVALID_ARG, "B = %lld < 0", (long long)d->B);
+  const int64_t v[10] = {d->Ci, d->Co, d->Nx, d->Ny, d->Nz, d->Nt, d->mx, d->my, d->mz, d->mt};
+  static const char* nm[10] = {"C_in", "C_out", "Nx", "Ny", "Nz", "Nt", "mx", "my", "mz", "mt"};
+  for (int q = 0; q < 10; ++q)
+    if (v[q] < 1) return fail(FNO_ERR_INVALID_ARG, "%s = %lld must be >= 1", nm[q], (long long)v[q]);
+  for (int q = 2; q < 6; ++q)
+    if (v[q] > (1 << 20)) return fail(FNO_ERR_INVALID_ARG, "%s = %lld too large", nm[q], (long long)v[q]);
+  if (2 * d->mx > d->Nx) return fail(FNO_ERR_INVALID_ARG, "2*mx = %lld > Nx = %lld", (long long)(2 * d->mx), (long long)d->Nx);
+  if (2 * d->my > d->Ny) return fail(FNO_ERR_INVALID_ARG, "2*my = %lld > Ny = %lld", (long long)(2 * d->my), (long long)d->Ny);
+  if (2 * d->mz > d->Nz) return fail(FNO_ERR_INVALID_ARG, "2*mz = %lld > Nz = %lld", (long long)(2 * d->mz), (long long)d->Nz);
+  if (d->mt > d->Nt / 2 + 1) return fail(FNO_ERR_INVALID_ARG, "mt = %lld > Nt/2 + 1 = %lld", (long long)d->mt, (long long)(d->Nt / 2 + 1));
+  d->Jx = 2 * d->mx;
+  d->Jy = 2 * d->my;
+  d->Jz = 2 * d->mz;
+  d->Jt = d->mt;
+  d->Ng = d->Nx * d->Ny * d->Nz * d->Nt;
+  d->Mk = d->Jx * d->Jy * d->Jz * d->Jt;
+  return FNO_OK;
+}
+
+static int check_support(const Dims& d, int precision, int op) {
+  if (precision < FNO_FP32 || precision > FNO_BF16X3)
+    return fail(FNO_ERR_INVALID_ARG, "precision %d is not an fno_precision", precision);
+  if (op < FNO_OP_SPECTRAL_FWD || op > FNO_OP_BLOCK_BWD)
+    return fail(FNO_ERR_INVALID_ARG, "op %d is not an fno_op", op);
+  if (precision != FNO_FP32)
+    return fail(FNO_ERR_UNSUPPORTED, "precision %d is not available in this build", precision);
+  if (d.Ci > kMaxChannels || d.Co > kMaxChannels)
+    return fail(FNO_ERR_UNSUPPORTED, "C_in, C_out must be <= %lld", (long long)kMaxChannels);
+  const size_t need[5] = {
+      fwd_tz_smem_bytes(d),
+      line_smem_bytes((int)d.Ny, (int)d.Jy),
+      line_smem_bytes((int)d.Nx, (int)d.Jx),
+      line_smem_bytes((int)d.Jx, (int)d.Nx),
+      line_smem_bytes((int)d.Jy, (int)d.Ny)};
+  for (size_t q = 0; q < 5; ++q)
+    if (need[q] > kMaxSmem)
+      return fail(FNO_ERR_UNSUPPORTED, "grid/mode sizes need %zu bytes of shared memory in a DFT stage", need[q]);
+  const int64_t Cm = d.Ci > d.Co ? d.Ci : d.Co;
+  size_t e = epilogue_smem_bytes(d, op == FNO_OP_BLOCK_BWD ? EPI_DA : EPI_FWD, (int)Cm, (int)Cm);
+  if (e > kMaxSmem)
+    return fail(FNO_ERR_UNSUPPORTED, "channel/grid sizes need %zu bytes of shared memory in the epilogue", e);
+  return FNO_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t tab[10];
+  size_t t1, t2, xh, yh, gxh, da, part, total;
+  bool da_in_dx;
+};
+
+static Layout layout(const Dims& d, int op) {
+  Layout L{};
+  size_t off = 0;
+  const int64_t tsz[10] = {d.Jx * d.Nx, d.Jy * d.Ny, d.Jz * d.Nz, d.Jt * d.Nt, d.Jt * d.Nt,
+                           d.Nx * d.Jx, d.Ny * d.Jy, d.Nz * d.Jz, d.Jt * d.Nt, d.Jt * d.Nt};
+  for (int q = 0; q < 10; ++q) {
+    L.tab[q] = off;
+    off += align256(sizeof(float2) * (size_t)tsz[q]);
+  }
+  const int64_t Cm = d.Ci > d.Co ? d.Ci : d.Co;
+  L.t1 = off;
+  off += align256(sizeof(float2) * (size_t)(d.B * Cm * d.Nx * d.Ny * d.Jz * d.Jt));
+  L.t2 = off;
+  off += align256(sizeof(float2) * (size_t)(d.B * Cm * d.Nx * d.Jy * d.Jz * d.Jt));
+  L.xh = off;
+  off += align256(sizeof(float2) * (size_t)(d.B * d.Ci * d.Mk));
+  L.yh = off;
+  off += align256(sizeof(float2) * (size_t)(d.B * d.Co * d.Mk));
+  if (op == FNO_OP_SPECTRAL_BWD || op == FNO_OP_BLOCK_BWD) {
+    L.gxh = off;
+    off += align256(sizeof(float2) * (size_t)(d.B * d.Ci * d.Mk));
+  }
+  if (op == FNO_OP_BLOCK_BWD) {
+    // dA lives in dx while dx is not yet written when the channel counts agree
+    L.da_in_dx = (d.Ci == d.Co);
+    if (!L.da_in_dx) {
+      L.da = off;
+      off += align256(sizeof(float) * (size_t)(d.B * d.Co * d.Ng));
+    }
+    L.part = off;
+    off += align256(sizeof(float) * (size_t)epilogue_max_grid() * (size_t)(d.Ci * d.Co + d.Co));
+  }
+  L.total = off;
+  return L;
+}
+
+static Tables tables_at(char* ws, const Layout& L) {
+  Tables T;
+  float2** p[10] = {&T.Fx, &T.Fy, &T.Fz, &T.Ft, &T.Fta, &T.Ix, &T.Iy, &T.Iz, &T.Its, &T.Itu};
+  for (int q = 0; q < 10; ++q) *p[q] = reinterpret_cast<float2*>(ws + L.tab[q]);
+  return T;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
+  if (ws_bytes < L.total)
+    return fail(FNO_ERR_WORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, L.total);
+  if (L.total > 0 && !ws) return fail(FNO_ERR_WORKSPACE, "workspace is NULL");
+  if (ws && !aligned(ws, 256)) return fail(FNO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  return FNO_OK;
+}
+
+#define REQ(ptr, al)                                                                  \
+  do {                                                                                \
+    if (!(ptr)) return fail(FNO_ERR_INVALID_ARG, "%s is NULL", #ptr);                \
+    if (!aligned((ptr), (al))) return fail(FNO_ERR_INVALID_ARG, "%s must be %d-byte aligned", #ptr, (int)(al)); \
+  } while (0)
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+// Forward kept-mode spectrum of C channels of src into out (FP32 path):
+// t,z per column -> y -> x.  Uses t1, t2.
+static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2* ft,
+                        const Tables& T, float2* t1, float2* t2, float2* out, cudaStream_t s) {
+  CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
+  CK(launch_line_f32(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, s));
+  CK(launch_line_f32(t2, out, d.B * C, (int)d.Nx, (int)d.Jx, d.Jy * d.Jz * d.Jt, T.Fx, s));
+  return FNO_OK;
+}
+
+// Inverse x then y of C channels of kept spectra into u1 = [B][C][Nx][Ny][Jz][Jt].
+static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tables& T, float2* t2,
+                          float2* u1, cudaStream_t s) {
+  CK(launch_line_f32(sp, t2, d.B * C, (int)d.Jx, (int)d.Nx, d.Jy * d.Jz * d.Jt, T.Ix, s));
+  CK(launch_line_f32(t2, u1, d.B * C * d.Nx, (int)d.Jy, (int)d.Ny, d.Jz * d.Jt, T.Iy, s));
+  return FNO_OK;
+}
+
+static int forward_common(const Dims& d, int precision, int op, const float* x, const float* w,
+                          const float* w_lin, const float* bias, float* out, void* ws,
+                          size_t ws_bytes, cudaStream_t s) {
+  int rc = check_support(d, precision, op);
+  if (rc) return rc;
+  const Layout L = layout(d, op);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  REQ(w, 8);
+  if (op == FNO_OP_BLOCK_FWD) {
+    REQ(w_lin, 4);
+    REQ(bias, 4);
+  }
+  if (d.B == 0) return FNO_OK;
+  REQ(x, 16);
+  REQ(out, 16);
+  char* base = static_cast<char*>(ws);
+  const Tables T = tables_at(base, L);
+  float2* t1 = reinterpret_cast<float2*>(base + L.t1);
+  float2* t2 = reinterpret_cast<float2*>(base + L.t2);
+  float2* xh = reinterpret_cast<float2*>(base + L.xh);
+  float2* yh = reinterpret_cast<float2*>(base + L.yh);
+  CK(launch_tables(d, T, s));
+  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s))) return rc;
+  CK(launch_mix_f32(d, xh, reinterpret_cast<const float2*>(w), yh, s));
+  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s))) return rc;
+  EpiArgs a{};
+  a.mode = (op == FNO_OP_BLOCK_FWD) ? EPI_FWD : EPI_SPECTRAL;
+  a.U = t1;
+  a.lin_in = x;
+  a.wlin = w_lin;
+  a.bias = bias;
+  a.out = out;
+  a.Iz = T.Iz;
+  a.It = T.Its;
+  a.Cs = (int)d.Co;
+  a.Cl = (op == FNO_OP_BLOCK_FWD) ? (int)d.Ci : 0;
+  a.w_si = (int)d.Co;
+  a.w_sc = 1;
+  CK(launch_epilogue_f32(d, a, nullptr, s));
+  return FNO_OK;
+}
+
+}  // namespace fno
+
+using namespace fno;
+
+extern "C" {
+
+size_t fno_workspace_bytes(const fno_dims* dims, int precision, int op) {
+  Dims d;
+  if (to_dims(dims, &d)) return 0;
+  if (check_support(d, precision, op)) return 0;
+  return layout(d, op).total;
+}
+
+int fno_spectral_fwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                     float* y, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  int rc = to_dims(dims, &d);
+  if (rc) return rc;
+  return forward_common(d, precision, FNO_OP_SPECTRAL_FWD, x, w, nullptr, nullptr, y, ws,
+                        ws_bytes, (cudaStream_t)stream);
+}
+
+int fno_block_fwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                  const float* w_lin, const float* bias, float* z, void* ws, size_t ws_bytes,
+                  void* stream) {
+  Dims d;
+  int rc = to_dims(dims, &d);
+  if (rc) return rc;
+  return forward_common(d, precision, FNO_OP_BLOCK_FWD, x, w, w_lin, bias, z, ws, ws_bytes,
+                        (cudaStream_t)stream);
+}
+
+int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                     const float* dy, float* dx, float* dw, void* ws, size_t ws_bytes,
+                     void* stream) {
+  Dims d;
+  int rc = to_dims(dims, &d);
+  if (rc) return rc;
+  const int op = FNO_OP_SPECTRAL_BWD;
+  if ((rc = check_support(d, precision, op))) return rc;
+  const Layout L = layout(d, op);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  if (!dx && !dw) return fail(FNO_ERR_INVALID_ARG, "dx and dw are both NULL");
+  REQ(w, 8);
+  if (dw && !aligned(dw, 8)) return fail(FNO_ERR_INVALID_ARG, "dw must be 8-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d.B == 0) {
+    if (dw) CK(launch_fill_zero(dw, 2 * d.Ci * d.Co * d.Mk, s));
+    return FNO_OK;
+  }
+  REQ(dy, 16);
+  if (dw) REQ(x, 16);
+  if (dx) REQ(dx, 16);
+  char* base = static_cast<char*>(ws);
+  const Tables T = tables_at(base, L);
+  float2* t1 = reinterpret_cast<float2*>(base + L.t1);
+  float2* t2 = reinterpret_cast<float2*>(base + L.t2);
+  float2* xh = reinterpret_cast<float2*>(base + L.xh);
+  float2* g = reinterpret_cast<float2*>(base + L.yh);
+  float2* gxh = reinterpret_cast<float2*>(base + L.gxh);
+  CK(launch_tables(d, T, s));
+  if ((rc = spectrum_f32(d, d.Co, dy, T.Fta, T, t1, t2, g, s))) return rc;
+  if (dw)
+    if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s))) return rc;
+  CK(launch_mix_adjoint_f32(d, xh, reinterpret_cast<const float2*>(w), g,
+                            reinterpret_cast<float2*>(dw), dx ? gxh : nullptr, s));
+  if (dx) {
+    if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s))) return rc;
+    EpiArgs a{};
+    a.mode = EPI_SPECTRAL;
+    a.U = t1;
+    a.out = dx;
+    a.Iz = T.Iz;
+    a.It = T.Itu;
+    a.Cs = (int)d.Ci;
+    a.Cl = 0;
+    CK(launch_epilogue_f32(d, a, nullptr, s));
+  }
+  return FNO_OK;
+}
+
+int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                  const float* w_lin, const float* bias, const float* dz, float* dx, float* dw,
+                  float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  int rc = to_dims(dims, &d);
+  if (rc) return rc;
+  const int op = FNO_OP_BLOCK_BWD;
+  if ((rc = check_support(d, precision, op))) return rc;
+  const Layout L = layout(d, op);
+  if ((rc = check_ws(ws, ws_bytes, L))) return rc;
+  REQ(w, 8);
+  REQ(w_lin, 4);
+  REQ(bias, 4);
+  REQ(dw, 8);
+  REQ(dw_lin, 4);
+  REQ(db, 4);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d.B == 0) {
+    CK(launch_fill_zero(dw, 2 * d.Ci * d.Co * d.Mk, s));
+    CK(launch_fill_zero(dw_lin, d.Ci * d.Co, s));
+    CK(launch_fill_zero(db, d.Co, s));
+    return FNO_OK;
+  }
+  REQ(x, 16);
+  REQ(dz, 16);
+  REQ(dx, 16);
+  char* base = static_cast<char*>(ws);
+  const Tables T = tables_at(base, L);
+  float2* t1 = reinterpret_cast<float2*>(base + L.t1);
+  float2* t2 = reinterpret_cast<float2*>(base + L.t2);
+  float2* xh = reinterpret_cast<float2*>(base + L.xh);
+  float2* yh = reinterpret_cast<float2*>(base + L.yh);
+  float2* gxh = reinterpret_cast<float2*>(base + L.gxh);
+  float* da = L.da_in_dx ? dx : reinterpret_cast<float*>(base + L.da);
+  float* part = reinterpret_cast<float*>(base + L.part);
+  const float2* wc = reinterpret_cast<const float2*>(w);
+
+  CK(launch_tables(d, T, s));
+  // recompute the forward spectrum and the spectral partial U1 of the output
+  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s))) return rc;
+  CK(launch_mix_f32(d, xh, wc, yh, s));
+  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s))) return rc;
+  // dA = dz GELU'(A) with the partial sums of dW_lin and db
+  EpiArgs a{};
+  a.mode = EPI_DA;
+  a.U = t1;
+  a.lin_in = x;
+  a.wlin = w_lin;
+  a.bias = bias;
+  a.dz = dz;
+  a.out = da;
+  a.part = part;
+  a.Iz = T.Iz;
+  a.It = T.Its;
+  a.Cs = (int)d.Co;
+  a.Cl = (int)d.Ci;
+  a.w_si = (int)d.Co;
+  a.w_sc = 1;
+  int rows = 0;
+  CK(launch_epilogue_f32(d, a, &rows, s));
+  CK(launch_reduce_partials(part, rows, (int)d.Ci, (int)d.Co, dw_lin, db, s));
+  // G = (c/N) DFT(dA); dW and the input-spectrum gradient
+  if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s))) return rc;
+  CK(launch_mix_adjoint_f32(d, xh, wc, yh, reinterpret_cast<float2*>(dw), gxh, s));
+  // dX = inverse(GXh) + W_lin dA
+  if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s))) return rc;
+  EpiArgs q{};
+  q.mode = EPI_DX;
+  q.U = t1;
+  q.lin_in = da;
+  q.wlin = w_lin;
+  q.out = dx;
+  q.Iz = T.Iz;
+  q.It = T.Itu;
+  q.Cs = (int)d.Ci;
+  q.Cl = (int)d.Co;
+  q.w_si = 1;
+  q.w_sc = (int)d.Co;
+  CK(launch_epilogue_f32(d, q, nullptr, s));
+  return FNO_OK;
+}
+
+const char* fno_last_error(void) { return g_err.c_str(); }
+
+int fno_version(void) { return 100; }
+
+int64_t fno_launch_count(void) { return g_launches.load(); }
+
+int fno_profile_start(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_recs.clear();
+  g_agg.clear();
+  g_pool_used = 0;
+  g_prof = true;
+  return FNO_OK;
+}
+
+int fno_profile_stop(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof = false;
+  g_agg.clear();
+  for (const ProfRec& r : g_recs) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    bool found = false;
+    for (ProfAgg& g : g_agg)
+      if (g.name == r.name) {
+        g.n += 1;
+        g.ms += ms;
+        found = true;
+        break;
+      }
+    if (!found) g_agg.push_back(ProfAgg{r.name, 1, (double)ms});
+  }
+  g_recs.clear();
+  g_pool_used = 0;
+  return FNO_OK;
+}
+
+int fno_profile_count(void) { return (int)g_agg.size(); }
+
+int fno_profile_entry(int i, const char** name, int64_t* launches, double* total_ms) {
+  if (i < 0 || i >= (int)g_agg.size()) return fail(FNO_ERR_INVALID_ARG, "profile entry %d out of range", i);
+  if (name) *name = g_agg[i].name.c_str();
+  if (launches) *launches = g_agg[i].n;
+  if (total_ms) *total_ms = g_agg[i].ms;
+  return FNO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// fno_internal.h -- declarations shared by the translation units of libfno.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fno.h"
+
+namespace fno {
+
+// Sizes with the derived mode counts.  Jx = 2mx, Jy = 2my, Jz = 2mz, Jt = mt;
+// Ng = grid points per channel, Mk = kept modes per channel.
+struct Dims {
+  int64_t B, Ci, Co, Nx, Ny, Nz, Nt, mx, my, mz, mt;
+  int64_t Jx, Jy, Jz, Jt, Ng, Mk;
+};
+
+// DFT basis tables in the workspace, FP32 complex (re, im), generated in FP64.
+//   forward  F?[j][n] = exp(-2 pi i k_j n / N?)          (Fx, Fy, Fz, Ft)
+//            Fta[j][t] = (c(kt)/N) exp(-2 pi i kt t / Nt)   (the adjoint scale of G)
+//   inverse  I?[n][j] = exp(+2 pi i k_j n / N?)          (Ix, Iy, Iz)
+//            Its[j][t] = (c(kt)/N) exp(+2 pi i kt t / Nt)   (the block's inverse)
+//            Itu[j][t] = exp(+2 pi i kt t / Nt)             (adjoint of the forward DFT)
+struct Tables {
+  float2 *Fx, *Fy, *Fz, *Ft, *Fta;
+  float2 *Ix, *Iy, *Iz, *Its, *Itu;
+};
+
+// ---- launch bookkeeping (fno_api.cu) --------------------------------------
+void prof_before(const char* name, cudaStream_t s);
+void prof_after(cudaStream_t s);
+int sm_count();
+
+// ---- FP32 CUDA-core kernels (fno_fp32.cu) -----------------------------------
+cudaError_t launch_tables(const Dims& d, const Tables& T, cudaStream_t s);
+
+// in[ncol][Nz][Nt] real -> out[ncol][Jz][Jt] complex: pruned DFT over t, then z.
+// ft is Ft or Fta.
+cudaError_t launch_fwd_tz_f32(const float* in, float2* out, int64_t ncol, const Dims& d,
+                              const float2* ft, const float2* fz, cudaStream_t s);
+
+// out[o][q][i] = sum_n tab[q][n] in[o][n][i] (complex), tab [nout][nin].
+cudaError_t launch_line_f32(const float2* in, float2* out, int64_t outer, int nin, int nout,
+                            int64_t inner, const float2* tab, cudaStream_t s);
+
+// yh[b][o][j] = sum_i xh[b][i][j] w[i][o][j]
+cudaError_t launch_mix_f32(const Dims& d, const float2* xh, const float2* w, float2* yh,
+                           cudaStream_t s);
+
+// dw[i][o][j] = sum_b conj(xh[b][i][j]) g[b][o][j] (nullable),
+// gxh[b][i][j] = sum_o conj(w[i][o][j]) g[b][o][j] (nullable)
+cudaError_t launch_mix_adjoint_f32(const Dims& d, const float2* xh, const float2* w,
+                                   const float2* g, float2* dw, float2* gxh, cudaStream_t s);
+
+enum EpiMode { EPI_SPECTRAL = 0, EPI_FWD = 1, EPI_DA = 2, EPI_DX = 3 };
+
+struct EpiArgs {
+  int mode;
+  const float2* U;      // [B][Cs][Nx][Ny][Jz][Jt]   spectrum after the inverse x, y stages
+  const float* lin_in;  // [B][Cl][grid]  x (FWD, DA) or dA (DX)
+  const float* wlin;    // [Ci][Co]
+  const float* bias;    // [Co]
+  const float* dz;      // [B][Co][grid] (DA)
+  float* out;           // [B][Cs][grid]
+  float* part;          // per-CTA partial sums of dWl and db (DA)
+  const float2* Iz;     // [Nz][Jz]
+  const float2* It;     // [Jt][Nt]  (Its or Itu)
+  int Cs, Cl;           // output (spectral) channels, linear-input channels
+  int w_si, w_sc;       // w_lin index of (linear-input channel i, output channel c) = i*w_si + c*w_sc
+};
+
+// Inverse z, t stages with the pointwise epilogue; returns the grid size used
+// (the number of partial rows written in EPI_DA mode).
+cudaError_t launch_epilogue_f32(const Dims& d, const EpiArgs& a, int* grid_used, cudaStream_t s);
+int epilogue_max_grid();
+size_t epilogue_smem_bytes(const Dims& d, int mode, int Cs, int Cl);
+size_t fwd_tz_smem_bytes(const Dims& d);
+size_t line_smem_bytes(int nin, int nout);
+
+// dwl[i][o] = sum_r part[r][i*Co+o], db[o] = sum_r part[r][Ci*Co+o]
+cudaError_t launch_reduce_partials(const float* part, int rows, int Ci, int Co, float* dwl,
+                                   float* db, cudaStream_t s);
+
+cudaError_t launch_fill_zero(float* p, int64_t n, cudaStream_t s);
+
+}  // namespace fno

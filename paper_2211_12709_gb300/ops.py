@@ -1,0 +1,196 @@
+"""PyTorch-facing wrappers of libfno (marshalling only: every step runs in the CUDA kernels).
+
+Tensors are FP32 CUDA tensors in the layouts of include/fno.h:
+  x  [B, C_in, Nx, Ny, Nz, Nt],  w [C_in, C_out, 2mx, 2my, 2mz, mt, 2] (re, im),
+  w_lin [C_in, C_out],  bias [C_out].
+``modes`` is (mx, my, mz, mt).  PyTorch provides device memory (outputs and the
+workspace come from its caching allocator) and the current stream.
+
+``SpectralConv4dFn`` and ``FNOBlock4dFn`` are autograd Functions whose backward
+calls the hand-written adjoint kernels.  The block keeps only its input between
+the passes (the backward recomputes the forward spectrum: per-block activation
+checkpointing), so a stack of blocks holds one activation per block.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+OP_SPECTRAL_FWD = _lib.FNO_OP_SPECTRAL_FWD
+OP_SPECTRAL_BWD = _lib.FNO_OP_SPECTRAL_BWD
+OP_BLOCK_FWD = _lib.FNO_OP_BLOCK_FWD
+OP_BLOCK_BWD = _lib.FNO_OP_BLOCK_BWD
+
+
+def precision_code(p) -> int:
+    if isinstance(p, int):
+        return p
+    try:
+        return _lib.PRECISIONS[p]
+    except KeyError:
+        raise ValueError(f"unknown precision {p!r}; one of {sorted(_lib.PRECISIONS)}") from None
+
+
+def dims_of(x: torch.Tensor, C_out: int, modes) -> _lib.fno_dims:
+    if x.dim() != 6:
+        raise ValueError(f"x must be [B, C, Nx, Ny, Nz, Nt], got shape {tuple(x.shape)}")
+    B, Ci, Nx, Ny, Nz, Nt = (int(v) for v in x.shape)
+    mx, my, mz, mt = (int(v) for v in modes)
+    return _lib.make_dims(B, Ci, C_out, Nx, Ny, Nz, Nt, mx, my, mz, mt)
+
+
+def _req(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor (libfno has no CPU path)")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.contiguous()
+
+
+def _stream_handle(dev) -> int:
+    return int(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def workspace(dims, precision, op, device) -> torch.Tensor:
+    n = _lib.fno_workspace_bytes(dims, precision_code(precision), op)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+
+
+def _wshape(Ci, Co, modes):
+    mx, my, mz, mt = modes
+    return (Ci, Co, 2 * mx, 2 * my, 2 * mz, mt, 2)
+
+
+def spectral_fwd(x, w, modes, precision="fp32", ws=None):
+    x = _req(x, "x")
+    Ci = x.shape[1]
+    Co = w.shape[1]
+    w = _req(w, "w", _wshape(Ci, Co, modes))
+    d = dims_of(x, Co, modes)
+    p = precision_code(precision)
+    y = torch.empty((x.shape[0], Co) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
+    if ws is None:
+        ws = workspace(d, p, OP_SPECTRAL_FWD, x.device)
+    _lib.fno_spectral_fwd(d, p, x.data_ptr(), w.data_ptr(), y.data_ptr(), ws.data_ptr(),
+                          ws.numel(), _stream_handle(x.device))
+    return y
+
+
+def spectral_bwd(x, w, dy, modes, need_dx=True, need_dw=True, precision="fp32", ws=None):
+    x = _req(x, "x")
+    Ci, Co = x.shape[1], w.shape[1]
+    w = _req(w, "w", _wshape(Ci, Co, modes))
+    dy = _req(dy, "dy", (x.shape[0], Co) + tuple(x.shape[2:]))
+    d = dims_of(x, Co, modes)
+    p = precision_code(precision)
+    dx = torch.empty_like(x) if need_dx else None
+    dw = torch.empty_like(w) if need_dw else None
+    if ws is None:
+        ws = workspace(d, p, OP_SPECTRAL_BWD, x.device)
+    _lib.fno_spectral_bwd(d, p, x.data_ptr(), w.data_ptr(), dy.data_ptr(),
+                          dx.data_ptr() if dx is not None else None,
+                          dw.data_ptr() if dw is not None else None,
+                          ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    return dx, dw
+
+
+def block_fwd(x, w, w_lin, bias, modes, precision="fp32", ws=None):
+    x = _req(x, "x")
+    Ci, Co = x.shape[1], w.shape[1]
+    w = _req(w, "w", _wshape(Ci, Co, modes))
+    w_lin = _req(w_lin, "w_lin", (Ci, Co))
+    bias = _req(bias, "bias", (Co,))
+    d = dims_of(x, Co, modes)
+    p = precision_code(precision)
+    z = torch.empty((x.shape[0], Co) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
+    if ws is None:
+        ws = workspace(d, p, OP_BLOCK_FWD, x.device)
+    _lib.fno_block_fwd(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(),
+                       z.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    return z
+
+
+def block_bwd(x, w, w_lin, bias, dz, modes, precision="fp32", ws=None):
+    x = _req(x, "x")
+    Ci, Co = x.shape[1], w.shape[1]
+    w = _req(w, "w", _wshape(Ci, Co, modes))
+    w_lin = _req(w_lin, "w_lin", (Ci, Co))
+    bias = _req(bias, "bias", (Co,))
+    dz = _req(dz, "dz", (x.shape[0], Co) + tuple(x.shape[2:]))
+    d = dims_of(x, Co, modes)
+    p = precision_code(precision)
+    dx = torch.empty_like(x)
+    dw = torch.empty_like(w)
+    dwl = torch.empty_like(w_lin)
+    db = torch.empty_like(bias)
+    if ws is None:
+        ws = workspace(d, p, OP_BLOCK_BWD, x.device)
+    _lib.fno_block_bwd(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(),
+                       dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(), db.data_ptr(),
+                       ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    return dx, dw, dwl, db
+
+
+class SpectralConv4dFn(torch.autograd.Function):
+    """y = S(x; w): truncated DFT, per-mode complex mixing, inverse DFT (Alg. 2)."""
+
+    @staticmethod
+    def forward(ctx, x, w, modes, precision="fp32"):
+        ctx.modes = tuple(int(m) for m in modes)
+        ctx.precision = precision
+        ctx.save_for_backward(x, w)
+        return spectral_fwd(x, w, ctx.modes, precision)
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, w = ctx.saved_tensors
+        dx, dw = spectral_bwd(x, w, dy.contiguous(), ctx.modes, ctx.needs_input_grad[0],
+                              ctx.needs_input_grad[1] or not ctx.needs_input_grad[0],
+                              ctx.precision)
+        return dx, (dw if ctx.needs_input_grad[1] else None), None, None
+
+
+class FNOBlock4dFn(torch.autograd.Function):
+    """z = GELU(S(x; w) + w_lin^T x + bias).  Only x is kept for the backward."""
+
+    @staticmethod
+    def forward(ctx, x, w, w_lin, bias, modes, precision="fp32"):
+        ctx.modes = tuple(int(m) for m in modes)
+        ctx.precision = precision
+        ctx.save_for_backward(x, w, w_lin, bias)
+        return block_fwd(x, w, w_lin, bias, ctx.modes, precision)
+
+    @staticmethod
+    def backward(ctx, dz):
+        x, w, w_lin, bias = ctx.saved_tensors
+        dx, dw, dwl, db = block_bwd(x, w, w_lin, bias, dz.contiguous(), ctx.modes, ctx.precision)
+        return dx, dw, dwl, db, None, None
+
+
+class FNOBlock4d(torch.nn.Module):
+    """One 4-D FNO block with its parameters (spectral weights, 1x1 weight, bias)."""
+
+    def __init__(self, width: int, modes, precision="fp32", device=None, seed=None):
+        super().__init__()
+        mx, my, mz, mt = (int(m) for m in modes)
+        self.modes = (mx, my, mz, mt)
+        self.precision = precision
+        g = torch.Generator(device="cpu")
+        if seed is not None:
+            g.manual_seed(int(seed))
+        scale = 1.0 / (width * width)
+        w = (torch.rand(_wshape(width, width, self.modes), generator=g) * 2 - 1) * scale
+        s = width ** -0.5
+        wl = (torch.rand((width, width), generator=g) * 2 - 1) * s
+        b = (torch.rand((width,), generator=g) * 2 - 1) * s
+        self.weight = torch.nn.Parameter(w.to(device))
+        self.w_lin = torch.nn.Parameter(wl.to(device))
+        self.bias = torch.nn.Parameter(b.to(device))
+
+    def forward(self, x):
+        return FNOBlock4dFn.apply(x, self.weight, self.w_lin, self.bias, self.modes, self.precision)

@@ -1,0 +1,101 @@
+"""Host-side checks of libfno that need no GPU: the library loads, exports every
+symbol include/fno.h declares, and rejects bad arguments before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2211_12709_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fno.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(fno_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_symbols()
+    for n in ("fno_spectral_fwd", "fno_spectral_bwd", "fno_block_fwd", "fno_block_bwd",
+              "fno_workspace_bytes", "fno_last_error"):
+        assert n in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = _lib.load()
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    assert set(declared_symbols()) <= set(_lib.EXPORTS) | {"fno_version"}
+    assert _lib.fno_version() >= 100
+
+
+def raw_ws(d, p, op):
+    return _lib.load().fno_workspace_bytes(ctypes.byref(d), p, op)
+
+
+def C1():
+    return _lib.make_dims(1, 8, 8, 16, 16, 16, 8, 4, 4, 4, 4)
+
+
+def test_workspace_query_is_deterministic_and_grows_with_batch():
+    a = _lib.fno_workspace_bytes(C1(), _lib.FNO_FP32, _lib.FNO_OP_BLOCK_BWD)
+    b = _lib.fno_workspace_bytes(C1(), _lib.FNO_FP32, _lib.FNO_OP_BLOCK_BWD)
+    assert a == b and a > 0 and a % 256 == 0
+    d2 = C1()
+    d2.B = 4
+    assert _lib.fno_workspace_bytes(d2, _lib.FNO_FP32, _lib.FNO_OP_BLOCK_BWD) > a
+    f = _lib.fno_workspace_bytes(C1(), _lib.FNO_FP32, _lib.FNO_OP_SPECTRAL_FWD)
+    assert 0 < f < a
+
+
+@pytest.mark.parametrize("field,value", [("Nx", 0), ("C_in", 0), ("mx", 9), ("mt", 6), ("B", -1),
+                                         ("mz", 0)])
+def test_invalid_dims_are_rejected_on_the_host(field, value):
+    d = C1()
+    setattr(d, field, value)
+    assert raw_ws(d, _lib.FNO_FP32, _lib.FNO_OP_BLOCK_FWD) == 0
+    lib = _lib.load()
+    rc = lib.fno_block_fwd(ctypes.byref(d), 0, None, None, None, None, None, None, 0, None)
+    assert rc == -1
+    assert _lib.fno_last_error()
+
+
+def test_null_and_misaligned_pointers_and_small_workspace_are_rejected():
+    lib = _lib.load()
+    d = C1()
+    need = _lib.fno_workspace_bytes(d, 0, _lib.FNO_OP_BLOCK_FWD)
+    # workspace too small: refused before touching any pointer
+    rc = lib.fno_block_fwd(ctypes.byref(d), 0, 256, 256, 256, 256, 256, 256, need - 256, None)
+    assert rc == -3
+    # misaligned workspace
+    rc = lib.fno_block_fwd(ctypes.byref(d), 0, 256, 256, 256, 256, 256, 257, need, None)
+    assert rc == -3
+    # null weights
+    rc = lib.fno_block_fwd(ctypes.byref(d), 0, 256, None, 256, 256, 256, 256, need, None)
+    assert rc == -1 and "w is NULL" in _lib.fno_last_error()
+    # misaligned x
+    rc = lib.fno_block_fwd(ctypes.byref(d), 0, 260, 256, 256, 256, 256, 256, need, None)
+    assert rc == -1 and "aligned" in _lib.fno_last_error()
+    # spectral backward needs at least one output
+    need_b = _lib.fno_workspace_bytes(d, 0, _lib.FNO_OP_SPECTRAL_BWD)
+    rc = lib.fno_spectral_bwd(ctypes.byref(d), 0, 256, 256, 256, None, None, 256, need_b, None)
+    assert rc == -1
+
+
+def test_bad_precision_and_op_codes():
+    assert raw_ws(C1(), 7, _lib.FNO_OP_BLOCK_FWD) == 0
+    assert raw_ws(C1(), 0, 9) == 0
+    lib = _lib.load()
+    rc = lib.fno_block_fwd(ctypes.byref(C1()), 7, 256, 256, 256, 256, 256, 256, 1 << 30, None)
+    assert rc == -1
+
+
+def test_too_many_channels_is_unsupported_not_a_crash():
+    d = C1()
+    d.C_in = 65
+    assert raw_ws(d, 0, _lib.FNO_OP_BLOCK_FWD) == 0
+    assert "<=" in _lib.fno_last_error()
