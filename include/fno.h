@@ -135,6 +135,34 @@ int fno_profile_stop(void);
 int fno_profile_count(void);
 int fno_profile_entry(int i, const char** name, int64_t* launches, double* total_ms);
 
+/* ---- allocation-free variant ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot hand the library a workspace: for example a host program whose own
+ * pool has reserved all device memory up front, or a runtime that forbids any
+ * device allocation once it has started, so neither it nor its plug-ins may call
+ * cudaMalloc to size a workspace.
+ *
+ * fno_spectral_fwd_static computes exactly what fno_spectral_fwd computes, but
+ * takes its scratch from a fixed array in the library's device memory
+ * (FNO_STATIC_SCRATCH_BYTES = 16 MiB, held on every GPU that loads the library
+ * until the process exits) instead of a caller workspace.  The caller still
+ * passes the input x, the weights w and the output y.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - Sizes whose fno_workspace_bytes(dims, precision, FNO_OP_SPECTRAL_FWD)
+ *     exceeds FNO_STATIC_SCRATCH_BYTES are refused with FNO_ERR_UNSUPPORTED
+ *     before anything is enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before capturing any stream.
+ *   - All calls share the one array and it keeps the previous call's contents;
+ *     every byte a call reads from it is written earlier in the same call, so
+ *     nothing needs clearing.  Calls that overlap on the GPU (other streams,
+ *     other host threads) race on the array: serialise them.
+ */
+#define FNO_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+int fno_spectral_fwd_static(const fno_dims* dims, int precision, const float* x, const float* w,
+                            float* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,8 +22,9 @@ PRECISIONS = {"fp32": FNO_FP32, "tf32": FNO_TF32, "bf16": FNO_BF16, "bf16x3": FN
 EXPORTS = (
     "fno_workspace_bytes", "fno_spectral_fwd", "fno_spectral_bwd", "fno_block_fwd",
     "fno_block_bwd", "fno_last_error", "fno_version", "fno_launch_count", "fno_profile_start",
-    "fno_profile_stop", "fno_profile_count", "fno_profile_entry",
+    "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static",
 )
+FNO_STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class fno_dims(ctypes.Structure):
@@ -63,6 +64,8 @@ def load(build_if_needed: bool = True):
         lib.fno_spectral_fwd.argtypes = [dp, ci, vp, vp, vp, vp, sz, vp]
         lib.fno_spectral_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_block_fwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, sz, vp]
+        lib.fno_spectral_fwd_static.argtypes = [dp, ci, vp, vp, vp, vp]
+        lib.fno_spectral_fwd_static.restype = ci
         lib.fno_block_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         for f in (lib.fno_spectral_fwd, lib.fno_spectral_bwd, lib.fno_block_fwd, lib.fno_block_bwd):
             f.restype = ci
@@ -108,6 +111,11 @@ def fno_workspace_bytes(dims: fno_dims, precision: int, op: int) -> int:
 def fno_spectral_fwd(dims, precision, x, w, y, ws, ws_bytes, stream=0):
     _check(load().fno_spectral_fwd(ctypes.byref(dims), int(precision), x, w, y, ws, ws_bytes,
                                    stream))
+
+
+def fno_spectral_fwd_static(dims, precision, x, w, y, stream=0):
+    """fno_spectral_fwd with the library's static device scratch (no workspace argument)."""
+    _check(load().fno_spectral_fwd_static(ctypes.byref(dims), int(precision), x, w, y, stream))
 
 
 def fno_spectral_bwd(dims, precision, x, w, dy, dx, dw, ws, ws_bytes, stream=0):

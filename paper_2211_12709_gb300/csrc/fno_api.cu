@@ -493,3 +493,54 @@ int fno_profile_entry(int i, const char** name, int64_t* launches, double* total
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free spectral forward: the scratch is a fixed device array of this
+// file instead of a caller workspace (for callers that may not allocate device
+// memory; see include/fno.h).
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_fno_static_scratch[FNO_STATIC_SCRATCH_BYTES];
+
+namespace fno {
+static std::mutex g_static_mu;
+static void* g_static_ptr[64] = {nullptr};
+
+// Device address of the static scratch on the current device.  The array's host
+// name is only a host-side stand-in, so the address is looked up once per
+// device with that device current and cached.
+static int static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(FNO_ERR_UNSUPPORTED, "device ordinal %d >= 64", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_fno_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    if (!p) return fail(FNO_ERR_CUDA, "cudaGetSymbolAddress returned NULL for the static scratch");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return FNO_OK;
+}
+}  // namespace fno
+
+extern "C" int fno_spectral_fwd_static(const fno_dims* dims, int precision, const float* x,
+                                       const float* w, float* y, void* stream) {
+  Dims d;
+  int rc = to_dims(dims, &d);
+  if (rc) return rc;
+  if ((rc = check_support(d, precision, FNO_OP_SPECTRAL_FWD))) return rc;
+  const size_t need = layout(d, FNO_OP_SPECTRAL_FWD).total;
+  if (need > FNO_STATIC_SCRATCH_BYTES)
+    return fail(FNO_ERR_UNSUPPORTED,
+                "these sizes need %zu bytes of scratch; the static scratch holds %zu bytes "
+                "(use fno_spectral_fwd with a workspace)",
+                need, (size_t)FNO_STATIC_SCRATCH_BYTES);
+  void* ws = nullptr;
+  if ((rc = static_scratch(&ws))) return rc;
+  return forward_common(d, precision, FNO_OP_SPECTRAL_FWD, x, w, nullptr, nullptr, y, ws,
+                        FNO_STATIC_SCRATCH_BYTES, (cudaStream_t)stream);
+}
+
