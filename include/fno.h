@@ -117,8 +117,17 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
                   const float* w_lin, const float* bias, const float* dz, float* dx, float* dw,
                   float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream);
 
+/* Status a previous call left in its workspace: waits for `stream`, then returns
+ * FNO_OK, or FNO_ERR_TIMEOUT when one of that call's bounded device-side waits
+ * (tensor-core pipeline barriers) gave up and the kernel returned early. */
+int fno_workspace_status(const void* ws, void* stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char* fno_last_error(void);
+
+/* fno_status of the calling thread's last failure (FNO_OK if none), e.g. to tell
+ * why fno_workspace_bytes() returned 0. */
+int fno_last_status(void);
 
 /* Library ABI version (major * 100 + minor). */
 int fno_version(void);

@@ -22,7 +22,7 @@ PRECISIONS = {"fp32": FNO_FP32, "tf32": FNO_TF32, "bf16": FNO_BF16, "bf16x3": FN
 EXPORTS = (
     "fno_workspace_bytes", "fno_spectral_fwd", "fno_spectral_bwd", "fno_block_fwd",
     "fno_block_bwd", "fno_last_error", "fno_version", "fno_launch_count", "fno_profile_start",
-    "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static",
+    "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static", "fno_workspace_status", "fno_last_status",
 )
 FNO_STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -69,6 +69,10 @@ def load(build_if_needed: bool = True):
         lib.fno_block_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         for f in (lib.fno_spectral_fwd, lib.fno_spectral_bwd, lib.fno_block_fwd, lib.fno_block_bwd):
             f.restype = ci
+        lib.fno_workspace_status.argtypes = [vp, vp]
+        lib.fno_workspace_status.restype = ci
+        lib.fno_last_status.argtypes = []
+        lib.fno_last_status.restype = ci
         lib.fno_last_error.argtypes = []
         lib.fno_last_error.restype = ctypes.c_char_p
         lib.fno_version.restype = ci
@@ -100,11 +104,10 @@ def fno_last_error() -> str:
 
 
 def fno_workspace_bytes(dims: fno_dims, precision: int, op: int) -> int:
-    n = load().fno_workspace_bytes(ctypes.byref(dims), int(precision), int(op))
+    lib = load()
+    n = lib.fno_workspace_bytes(ctypes.byref(dims), int(precision), int(op))
     if n == 0:
-        msg = fno_last_error()
-        if msg:
-            raise FnoError(-1, msg)
+        raise FnoError(int(lib.fno_last_status()), fno_last_error())
     return int(n)
 
 
@@ -132,6 +135,11 @@ def fno_block_bwd(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws
                   stream=0):
     _check(load().fno_block_bwd(ctypes.byref(dims), int(precision), x, w, w_lin, bias, dz, dx, dw,
                                 dw_lin, db, ws, ws_bytes, stream))
+
+
+def fno_workspace_status(ws, stream=0):
+    """Raise FnoError(FNO_ERR_TIMEOUT) if the call that used ws hit a bounded-wait timeout."""
+    _check(load().fno_workspace_status(ws, stream))
 
 
 def fno_version() -> int:

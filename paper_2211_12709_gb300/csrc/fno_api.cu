@@ -22,6 +22,7 @@
 namespace fno {
 
 static thread_local std::string g_err;
+static thread_local int g_status = FNO_OK;
 static std::atomic<int64_t> g_launches{0};
 
 static int fail(int code, const char* fmt, ...) {
@@ -31,6 +32,7 @@ static int fail(int code, const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_err = buf;
+  g_status = code;
   return code;
 }
 
@@ -126,8 +128,23 @@ static int check_support(const Dims& d, int precision, int op) {
     return fail(FNO_ERR_INVALID_ARG, "precision %d is not an fno_precision", precision);
   if (op < FNO_OP_SPECTRAL_FWD || op > FNO_OP_BLOCK_BWD)
     return fail(FNO_ERR_INVALID_ARG, "op %d is not an fno_op", op);
-  if (precision != FNO_FP32)
-    return fail(FNO_ERR_UNSUPPORTED, "precision %d is not available in this build", precision);
+  if (precision == FNO_TF32)
+    return fail(FNO_ERR_UNSUPPORTED, "precision FNO_TF32 is not available in this build");
+  if (precision == FNO_BF16 || precision == FNO_BF16X3) {
+    char why[256];
+    if (!fwd_tz_tc_supported(d, why, sizeof(why))) return fail(FNO_ERR_UNSUPPORTED, "%s", why);
+    const int modes[2][2] = {{EPI_SPECTRAL, EPI_SPECTRAL}, {EPI_FWD, EPI_DA}};
+    const bool block = (op == FNO_OP_BLOCK_FWD || op == FNO_OP_BLOCK_BWD);
+    for (int q = 0; q < 2; ++q) {
+      const int mode = modes[block ? 1 : 0][q];
+      if (!epilogue_tc_supported(d, mode, (int)d.Co, (int)d.Ci, why, sizeof(why)))
+        return fail(FNO_ERR_UNSUPPORTED, "%s", why);
+    }
+    if (op == FNO_OP_BLOCK_BWD && !epilogue_tc_supported(d, EPI_DX, (int)d.Ci, (int)d.Co, why, sizeof(why)))
+      return fail(FNO_ERR_UNSUPPORTED, "%s", why);
+    if (op == FNO_OP_SPECTRAL_BWD && !epilogue_tc_supported(d, EPI_SPECTRAL, (int)d.Ci, 0, why, sizeof(why)))
+      return fail(FNO_ERR_UNSUPPORTED, "%s", why);
+  }
   if (d.Ci > kMaxChannels || d.Co > kMaxChannels)
     return fail(FNO_ERR_UNSUPPORTED, "C_in, C_out must be <= %lld", (long long)kMaxChannels);
   const size_t need[5] = {
@@ -149,6 +166,7 @@ static int check_support(const Dims& d, int precision, int op) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
+  size_t err;  // device status word (nonzero: a bounded wait gave up)
   size_t tab[10];
   size_t t1, t2, xh, yh, gxh, da, part, total;
   bool da_in_dx;
@@ -157,6 +175,8 @@ struct Layout {
 static Layout layout(const Dims& d, int op) {
   Layout L{};
   size_t off = 0;
+  L.err = off;
+  off += 256;
   const int64_t tsz[10] = {d.Jx * d.Nx, d.Jy * d.Ny, d.Jz * d.Nz, d.Jt * d.Nt, d.Jt * d.Nt,
                            d.Nx * d.Jx, d.Ny * d.Jy, d.Nz * d.Jz, d.Jt * d.Nt, d.Jt * d.Nt};
   for (int q = 0; q < 10; ++q) {
@@ -184,7 +204,8 @@ static Layout layout(const Dims& d, int op) {
       off += align256(sizeof(float) * (size_t)(d.B * d.Co * d.Ng));
     }
     L.part = off;
-    off += align256(sizeof(float) * (size_t)epilogue_max_grid() * (size_t)(d.Ci * d.Co + d.Co));
+    const int rows = epilogue_max_grid() > epilogue_tc_max_grid() ? epilogue_max_grid() : epilogue_tc_max_grid();
+    off += align256(sizeof(float) * (size_t)rows * (size_t)(d.Ci * d.Co + d.Co));
   }
   L.total = off;
   return L;
@@ -219,11 +240,17 @@ static int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
   } while (0)
 
-// Forward kept-mode spectrum of C channels of src into out (FP32 path):
-// t,z per column -> y -> x.  Uses t1, t2.
+static bool is_tc(int precision) { return precision == FNO_BF16 || precision == FNO_BF16X3; }
+
+// Forward kept-mode spectrum of C channels of src into out: t,z per column
+// (tensor cores for the BF16 precisions) -> y -> x.  Uses t1, t2.
 static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2* ft,
-                        const Tables& T, float2* t1, float2* t2, float2* out, cudaStream_t s) {
-  CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
+                        const Tables& T, float2* t1, float2* t2, float2* out, cudaStream_t s,
+                        int precision = FNO_FP32, int* err = nullptr) {
+  if (is_tc(precision))
+    CK(launch_fwd_tz_tc(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, precision == FNO_BF16X3, err, s));
+  else
+    CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
   CK(launch_line_f32(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, s));
   CK(launch_line_f32(t2, out, d.B * C, (int)d.Nx, (int)d.Jx, d.Jy * d.Jz * d.Jt, T.Fx, s));
   return FNO_OK;
@@ -235,6 +262,12 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
   CK(launch_line_f32(sp, t2, d.B * C, (int)d.Jx, (int)d.Nx, d.Jy * d.Jz * d.Jt, T.Ix, s));
   CK(launch_line_f32(t2, u1, d.B * C * d.Nx, (int)d.Jy, (int)d.Ny, d.Jz * d.Jt, T.Iy, s));
   return FNO_OK;
+}
+
+static cudaError_t epilogue(const Dims& d, const EpiArgs& a, int precision, int* err, int* grid_used,
+                            cudaStream_t s) {
+  if (is_tc(precision)) return launch_epilogue_tc(d, a, precision == FNO_BF16X3, err, grid_used, s);
+  return launch_epilogue_f32(d, a, grid_used, s);
 }
 
 static int forward_common(const Dims& d, int precision, int op, const float* x, const float* w,
@@ -258,8 +291,9 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   float2* t2 = reinterpret_cast<float2*>(base + L.t2);
   float2* xh = reinterpret_cast<float2*>(base + L.xh);
   float2* yh = reinterpret_cast<float2*>(base + L.yh);
-  CK(launch_tables(d, T, s));
-  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s))) return rc;
+  int* err = reinterpret_cast<int*>(base + L.err);
+  CK(launch_tables(d, T, err, s));
+  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
   CK(launch_mix_f32(d, xh, reinterpret_cast<const float2*>(w), yh, s));
   if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s))) return rc;
   EpiArgs a{};
@@ -275,7 +309,7 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   a.Cl = (op == FNO_OP_BLOCK_FWD) ? (int)d.Ci : 0;
   a.w_si = (int)d.Co;
   a.w_sc = 1;
-  CK(launch_epilogue_f32(d, a, nullptr, s));
+  CK(epilogue(d, a, precision, err, nullptr, s));
   return FNO_OK;
 }
 
@@ -339,10 +373,11 @@ int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const 
   float2* xh = reinterpret_cast<float2*>(base + L.xh);
   float2* g = reinterpret_cast<float2*>(base + L.yh);
   float2* gxh = reinterpret_cast<float2*>(base + L.gxh);
-  CK(launch_tables(d, T, s));
-  if ((rc = spectrum_f32(d, d.Co, dy, T.Fta, T, t1, t2, g, s))) return rc;
+  int* err = reinterpret_cast<int*>(base + L.err);
+  CK(launch_tables(d, T, err, s));
+  if ((rc = spectrum_f32(d, d.Co, dy, T.Fta, T, t1, t2, g, s, precision, err))) return rc;
   if (dw)
-    if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s))) return rc;
+    if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
   CK(launch_mix_adjoint_f32(d, xh, reinterpret_cast<const float2*>(w), g,
                             reinterpret_cast<float2*>(dw), dx ? gxh : nullptr, s));
   if (dx) {
@@ -355,7 +390,7 @@ int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const 
     a.It = T.Itu;
     a.Cs = (int)d.Ci;
     a.Cl = 0;
-    CK(launch_epilogue_f32(d, a, nullptr, s));
+    CK(epilogue(d, a, precision, err, nullptr, s));
   }
   return FNO_OK;
 }
@@ -397,9 +432,10 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   float* part = reinterpret_cast<float*>(base + L.part);
   const float2* wc = reinterpret_cast<const float2*>(w);
 
-  CK(launch_tables(d, T, s));
+  int* err = reinterpret_cast<int*>(base + L.err);
+  CK(launch_tables(d, T, err, s));
   // recompute the forward spectrum and the spectral partial U1 of the output
-  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s))) return rc;
+  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
   CK(launch_mix_f32(d, xh, wc, yh, s));
   if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s))) return rc;
   // dA = dz GELU'(A) with the partial sums of dW_lin and db
@@ -419,10 +455,10 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   a.w_si = (int)d.Co;
   a.w_sc = 1;
   int rows = 0;
-  CK(launch_epilogue_f32(d, a, &rows, s));
+  CK(epilogue(d, a, precision, err, &rows, s));
   CK(launch_reduce_partials(part, rows, (int)d.Ci, (int)d.Co, dw_lin, db, s));
   // G = (c/N) DFT(dA); dW and the input-spectrum gradient
-  if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s))) return rc;
+  if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s, precision, err))) return rc;
   CK(launch_mix_adjoint_f32(d, xh, wc, yh, reinterpret_cast<float2*>(dw), gxh, s));
   // dX = inverse(GXh) + W_lin dA
   if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s))) return rc;
@@ -438,11 +474,25 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   q.Cl = (int)d.Co;
   q.w_si = 1;
   q.w_sc = (int)d.Co;
-  CK(launch_epilogue_f32(d, q, nullptr, s));
+  CK(epilogue(d, q, precision, err, nullptr, s));
+  return FNO_OK;
+}
+
+int fno_workspace_status(const void* ws, void* stream) {
+  if (!ws) return fail(FNO_ERR_INVALID_ARG, "ws is NULL");
+  int h = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(status)");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (h != 0) return fail(FNO_ERR_TIMEOUT, "a bounded device-side wait gave up (status %d)", h);
   return FNO_OK;
 }
 
 const char* fno_last_error(void) { return g_err.c_str(); }
+
+int fno_last_status(void) { return g_status; }
 
 int fno_version(void) { return 100; }
 

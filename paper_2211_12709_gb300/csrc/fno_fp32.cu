@@ -56,10 +56,12 @@ struct TabParams {
   int nseg;
   int Nt;
   double invNg;
+  int* err;
 };
 
 __global__ void k_tables(TabParams p) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx == 0 && p.err) *p.err = 0;
   if (idx >= p.start[p.nseg]) return;
   int s = 0;
   while (s + 1 < p.nseg && idx >= p.start[s + 1]) ++s;
@@ -81,8 +83,9 @@ __global__ void k_tables(TabParams p) {
   g.dst[e] = make_float2((float)(cs * sc), (float)((double)g.sign * sn * sc));
 }
 
-cudaError_t launch_tables(const Dims& d, const Tables& T, cudaStream_t s) {
+cudaError_t launch_tables(const Dims& d, const Tables& T, int* err, cudaStream_t s) {
   TabParams p{};
+  p.err = err;
   auto add = [&](float2* dst, int64_t rows, int64_t cols, int64_t N, int64_t m, int kr, int sign,
                  int scale) {
     p.seg[p.nseg] = TabSeg{dst, (int)rows, (int)cols, (int)N, (int)m, kr, sign, scale};
@@ -404,14 +407,6 @@ cudaError_t launch_mix_adjoint_f32(const Dims& d, const float2* xh, const float2
 //            DA: out = dz GELU'(S + lin + bias)      DX: out = S + lin
 //   phase 3  (DA) per-CTA sums of x_i dA_c and dA_c, Kahan-compensated
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float gelu_f(float a) {
-  return 0.5f * a * (1.0f + erff(a * 0.70710678118654752440f));
-}
-__device__ __forceinline__ float gelu_grad_f(float a) {
-  return 0.5f * (1.0f + erff(a * 0.70710678118654752440f)) +
-         a * expf(-0.5f * a * a) * 0.39894228040143267794f;
-}
-
 struct EpiK {
   EpiArgs a;
   long long B, Nx, Ny;

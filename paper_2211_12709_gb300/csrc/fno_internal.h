@@ -32,7 +32,8 @@ void prof_after(cudaStream_t s);
 int sm_count();
 
 // ---- FP32 CUDA-core kernels (fno_fp32.cu) -----------------------------------
-cudaError_t launch_tables(const Dims& d, const Tables& T, cudaStream_t s);
+// also clears the device status word *err of the call
+cudaError_t launch_tables(const Dims& d, const Tables& T, int* err, cudaStream_t s);
 
 // in[ncol][Nz][Nt] real -> out[ncol][Jz][Jt] complex: pruned DFT over t, then z.
 // ft is Ft or Fta.
@@ -82,5 +83,30 @@ cudaError_t launch_reduce_partials(const float* part, int rows, int Ci, int Co, 
                                    float* db, cudaStream_t s);
 
 cudaError_t launch_fill_zero(float* p, int64_t n, cudaStream_t s);
+
+// ---- tensor-core path (fno_tc.cu) -------------------------------------------
+// Pruned DFT over t then z on tcgen05 (BF16 or split BF16); same contract as
+// launch_fwd_tz_f32.  err: device word set to nonzero when a bounded wait gives up.
+bool fwd_tz_tc_supported(const Dims& d, char* why, size_t nwhy);
+cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const Dims& d,
+                             const float2* ft, const float2* fz, bool split, int* err,
+                             cudaStream_t s);
+
+// Inverse z, t and the pointwise epilogue on tcgen05; same contract as
+// launch_epilogue_f32 (EPI_DA writes epilogue_tc_max_grid() partial rows at most).
+bool epilogue_tc_supported(const Dims& d, int mode, int Cs, int Cl, char* why, size_t nwhy);
+cudaError_t launch_epilogue_tc(const Dims& d, const EpiArgs& a, bool split, int* err,
+                               int* grid_used, cudaStream_t s);
+int epilogue_tc_max_grid();
+
+#ifdef __CUDACC__
+__device__ __forceinline__ float gelu_f(float a) {
+  return 0.5f * a * (1.0f + erff(a * 0.70710678118654752440f));
+}
+__device__ __forceinline__ float gelu_grad_f(float a) {
+  return 0.5f * (1.0f + erff(a * 0.70710678118654752440f)) +
+         a * expf(-0.5f * a * a) * 0.39894228040143267794f;
+}
+#endif
 
 }  // namespace fno

@@ -22,6 +22,15 @@ OP_SPECTRAL_BWD = _lib.FNO_OP_SPECTRAL_BWD
 OP_BLOCK_FWD = _lib.FNO_OP_BLOCK_FWD
 OP_BLOCK_BWD = _lib.FNO_OP_BLOCK_BWD
 
+# When set, every call waits for its stream and raises if a device-side bounded
+# wait gave up (FNO_ERR_TIMEOUT).  For tests and debugging; off by default.
+CHECK_STATUS = False
+
+
+def _status(ws, dev):
+    if CHECK_STATUS:
+        _lib.fno_workspace_status(ws.data_ptr(), _stream_handle(dev))
+
 
 def precision_code(p) -> int:
     if isinstance(p, int):
@@ -78,6 +87,7 @@ def spectral_fwd(x, w, modes, precision="fp32", ws=None):
         ws = workspace(d, p, OP_SPECTRAL_FWD, x.device)
     _lib.fno_spectral_fwd(d, p, x.data_ptr(), w.data_ptr(), y.data_ptr(), ws.data_ptr(),
                           ws.numel(), _stream_handle(x.device))
+    _status(ws, x.device)
     return y
 
 
@@ -96,6 +106,7 @@ def spectral_bwd(x, w, dy, modes, need_dx=True, need_dw=True, precision="fp32", 
                           dx.data_ptr() if dx is not None else None,
                           dw.data_ptr() if dw is not None else None,
                           ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    _status(ws, x.device)
     return dx, dw
 
 
@@ -112,6 +123,7 @@ def block_fwd(x, w, w_lin, bias, modes, precision="fp32", ws=None):
         ws = workspace(d, p, OP_BLOCK_FWD, x.device)
     _lib.fno_block_fwd(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(),
                        z.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    _status(ws, x.device)
     return z
 
 
@@ -133,6 +145,7 @@ def block_bwd(x, w, w_lin, bias, dz, modes, precision="fp32", ws=None):
     _lib.fno_block_bwd(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(),
                        dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(), db.data_ptr(),
                        ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    _status(ws, x.device)
     return dx, dw, dwl, db
 
 

@@ -1,0 +1,127 @@
+"""Tensor-core precisions (BF16, split BF16) of the CUDA path vs the FP64 oracle.
+
+Tolerances (rel-L2 per tensor): split BF16 <= 1e-5, BF16 <= 2e-2.  Every call
+also checks the device status word: no bounded device-side wait gave up.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Dims
+from paper_2211_12709_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 1e-5, "bf16": 2e-2}
+
+
+@pytest.fixture(autouse=True)
+def _check_status():
+    from paper_2211_12709_gb300 import ops
+    old = ops.CHECK_STATUS
+    ops.CHECK_STATUS = True
+    yield
+    ops.CHECK_STATUS = old
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0))
+
+
+def make_case(d, cfg, field="normal"):
+    if field == "grf":
+        x = inputs.grf((d.B, d.Ci), d.grid, (8.0, 8.0, 8.0, 8.0), inputs.SEED_INPUT + cfg)
+    else:
+        x = inputs.normal((d.B, d.Ci) + d.grid, inputs.SEED_INPUT + cfg)
+    w = inputs.spectral_weights(d.Ci, d.Co, d.modes, inputs.SEED_SPECTRAL_W + cfg)
+    wl, b = inputs.linear_params(d.Ci, d.Co, inputs.SEED_LINEAR + cfg)
+    dz = inputs.normal((d.B, d.Co) + d.grid, inputs.SEED_UPSTREAM + cfg)
+    return x, w, wl, b, dz
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy() if t is not None else None
+
+
+def modes_of(d):
+    return (d.mx, d.my, d.mz, d.mt)
+
+
+TC_CASES = [
+    (Dims(1, 8, 8, 16, 16, 16, 8, 4, 4, 4, 4), "single-layer 16^3x8"),
+    (Dims(3, 5, 7, 12, 10, 32, 16, 3, 2, 8, 6), "Ci!=Co, Nz=32, Nt=16, ragged column groups"),
+    (Dims(2, 17, 9, 6, 5, 64, 32, 2, 2, 12, 8), "17->9 channels, Nz=64, Nt=32, 2mz=24"),
+    (Dims(1, 3, 4, 4, 4, 128, 8, 1, 1, 3, 5), "Nz=128, Nt=8, mt=Nt/2+1 (Nyquist)"),
+    (Dims(2, 20, 20, 8, 8, 8, 16, 2, 3, 4, 3), "Nz=8 (16 columns per tile), 2mz=Nz"),
+]
+
+
+@pytest.mark.parametrize("d,label", TC_CASES, ids=[c[1] for c in TC_CASES])
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+def test_tc_block_matches_oracle(d, label, precision):
+    from paper_2211_12709_gb300 import ops
+    x, w, wl, b, dz = make_case(d, 11)
+    X, W, WL, Bb, DZ = gpu(x), gpu(w), gpu(wl), gpu(b), gpu(dz)
+    z = ops.block_fwd(X, W, WL, Bb, modes_of(d), precision)
+    dx, dw, dwl, db = ops.block_bwd(X, W, WL, Bb, DZ, modes_of(d), precision)
+    torch.cuda.synchronize()
+    rz, _ = oracle.block_fwd(d, x, w, wl, b)
+    rg = oracle.block_bwd(d, x, w, dz, wl, b)
+    errs = {"z": relerr(host(z), rz), "dx": relerr(host(dx), rg["dx"]),
+            "dw": relerr(host(dw), rg["dw"]), "dwl": relerr(host(dwl), rg["dwl"]),
+            "db": relerr(host(db), rg["db"])}
+    print(label, precision, errs)
+    assert all(v <= TOL[precision] for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("d,label", TC_CASES[:3], ids=[c[1] for c in TC_CASES[:3]])
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+def test_tc_spectral_conv_matches_oracle(d, label, precision):
+    from paper_2211_12709_gb300 import ops
+    x, w, _, _, dy = make_case(d, 12)
+    X, W, DY = gpu(x), gpu(w), gpu(dy)
+    y = ops.spectral_fwd(X, W, modes_of(d), precision)
+    dx, dw = ops.spectral_bwd(X, W, DY, modes_of(d), True, True, precision)
+    torch.cuda.synchronize()
+    ry, _ = oracle.block_fwd(d, x, w)
+    rg = oracle.block_bwd(d, x, w, dy)
+    errs = {"y": relerr(host(y), ry), "dx": relerr(host(dx), rg["dx"]), "dw": relerr(host(dw), rg["dw"])}
+    print(label, precision, errs)
+    assert all(v <= TOL[precision] for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+def test_tc_full_block_grf_64cube(precision):
+    # 2 x 20 channels of a 64^3 x 16 smooth GRF (correlation 8 cells), modes 8/8/8/6
+    from paper_2211_12709_gb300 import ops
+    d = Dims(2, 20, 20, 64, 64, 64, 16, 8, 8, 8, 6)
+    x, w, wl, b, dz = make_case(d, 2, field="grf")
+    X, W, WL, Bb, DZ = gpu(x), gpu(w), gpu(wl), gpu(b), gpu(dz)
+    z = ops.block_fwd(X, W, WL, Bb, modes_of(d), precision)
+    dx, dw, dwl, db = ops.block_bwd(X, W, WL, Bb, DZ, modes_of(d), precision)
+    torch.cuda.synchronize()
+    rz, _ = oracle.block_fwd(d, x, w, wl, b)
+    rg = oracle.block_bwd(d, x, w, dz, wl, b)
+    errs = {"z": relerr(host(z), rz), "dx": relerr(host(dx), rg["dx"]),
+            "dw": relerr(host(dw), rg["dw"]), "dwl": relerr(host(dwl), rg["dwl"]),
+            "db": relerr(host(db), rg["db"])}
+    print("64^3x16 block errors", precision, errs)
+    assert all(v <= TOL[precision] for v in errs.values()), errs
+
+
+def test_tc_unsupported_shapes_are_refused_not_run():
+    from paper_2211_12709_gb300 import _lib, ops
+    x = torch.zeros((1, 2, 8, 8, 12, 6), device="cuda")   # Nz=12 does not divide 128
+    w = torch.zeros((2, 2, 4, 4, 4, 3, 2), device="cuda")
+    with pytest.raises(_lib.FnoError) as ei:
+        ops.spectral_fwd(x, w, (2, 2, 2, 3), "bf16x3")
+    assert ei.value.status == -2
