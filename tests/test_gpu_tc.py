@@ -61,7 +61,7 @@ TC_CASES = [
     (Dims(3, 5, 7, 12, 10, 32, 16, 3, 2, 8, 6), "Ci!=Co, Nz=32, Nt=16, ragged column groups"),
     (Dims(2, 17, 9, 6, 5, 64, 32, 2, 2, 12, 8), "17->9 channels, Nz=64, Nt=32, 2mz=24"),
     (Dims(1, 3, 4, 4, 4, 128, 8, 1, 1, 3, 5), "Nz=128, Nt=8, mt=Nt/2+1 (Nyquist)"),
-    (Dims(2, 20, 20, 8, 8, 8, 16, 2, 3, 4, 3), "Nz=8 (16 columns per tile), 2mz=Nz"),
+    (Dims(2, 20, 20, 8, 8, 16, 16, 2, 3, 8, 3), "Nz=16 (8 columns per tile), 2mz=Nz"),
 ]
 
 
@@ -120,7 +120,7 @@ def test_tc_full_block_grf_64cube(precision):
 
 def test_tc_unsupported_shapes_are_refused_not_run():
     from paper_2211_12709_gb300 import _lib, ops
-    x = torch.zeros((1, 2, 8, 8, 12, 6), device="cuda")   # Nz=12 does not divide 128
+    x = torch.zeros((1, 2, 8, 8, 12, 8), device="cuda")   # Nz=12 is not a tensor-core column height
     w = torch.zeros((2, 2, 4, 4, 4, 3, 2), device="cuda")
     with pytest.raises(_lib.FnoError) as ei:
         ops.spectral_fwd(x, w, (2, 2, 2, 3), "bf16x3")
