@@ -133,17 +133,6 @@ static int check_support(const Dims& d, int precision, int op) {
   if (precision == FNO_BF16 || precision == FNO_BF16X3) {
     char why[256];
     if (!fwd_tz_tc_supported(d, why, sizeof(why))) return fail(FNO_ERR_UNSUPPORTED, "%s", why);
-    const int modes[2][2] = {{EPI_SPECTRAL, EPI_SPECTRAL}, {EPI_FWD, EPI_DA}};
-    const bool block = (op == FNO_OP_BLOCK_FWD || op == FNO_OP_BLOCK_BWD);
-    for (int q = 0; q < 2; ++q) {
-      const int mode = modes[block ? 1 : 0][q];
-      if (!epilogue_tc_supported(d, mode, (int)d.Co, (int)d.Ci, why, sizeof(why)))
-        return fail(FNO_ERR_UNSUPPORTED, "%s", why);
-    }
-    if (op == FNO_OP_BLOCK_BWD && !epilogue_tc_supported(d, EPI_DX, (int)d.Ci, (int)d.Co, why, sizeof(why)))
-      return fail(FNO_ERR_UNSUPPORTED, "%s", why);
-    if (op == FNO_OP_SPECTRAL_BWD && !epilogue_tc_supported(d, EPI_SPECTRAL, (int)d.Ci, 0, why, sizeof(why)))
-      return fail(FNO_ERR_UNSUPPORTED, "%s", why);
   }
   if (d.Ci > kMaxChannels || d.Co > kMaxChannels)
     return fail(FNO_ERR_UNSUPPORTED, "C_in, C_out must be <= %lld", (long long)kMaxChannels);
@@ -204,7 +193,7 @@ static Layout layout(const Dims& d, int op) {
       off += align256(sizeof(float) * (size_t)(d.B * d.Co * d.Ng));
     }
     L.part = off;
-    const int rows = epilogue_max_grid() > epilogue_tc_max_grid() ? epilogue_max_grid() : epilogue_tc_max_grid();
+    const int rows = epilogue_max_grid();
     off += align256(sizeof(float) * (size_t)rows * (size_t)(d.Ci * d.Co + d.Co));
   }
   L.total = off;
@@ -264,9 +253,12 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
   return FNO_OK;
 }
 
+// The fused inverse z, t + epilogue stage runs in FP32 on the CUDA cores for
+// every precision (see fno_tc.cu for the measured reason).
 static cudaError_t epilogue(const Dims& d, const EpiArgs& a, int precision, int* err, int* grid_used,
                             cudaStream_t s) {
-  if (is_tc(precision)) return launch_epilogue_tc(d, a, precision == FNO_BF16X3, err, grid_used, s);
+  (void)precision;
+  (void)err;
   return launch_epilogue_f32(d, a, grid_used, s);
 }
 

@@ -397,212 +397,410 @@ cudaError_t launch_mix_adjoint_f32(const Dims& d, const float2* xh, const float2
 }
 
 // ---------------------------------------------------------------------------
-// Inverse z, t stages fused with the pointwise epilogue.
-// A CTA owns one (b, x, y) column at a time and all its channels.  For each
-// chunk of zc z-planes:
-//   phase 1  Q[c][z][jt] = sum_jz Iz[z][jz] U[c][jz][jt]
-//   phase 2  one thread per point (z, t):
-//            S_c = sum_jt Re(Q[c][z][jt] It[jt][t]),  lin_c = sum_i Wl(i, c) L_i
-//            SPECTRAL: out = S      FWD: out = GELU(S + lin + bias)
-//            DA: out = dz GELU'(S + lin + bias)      DX: out = S + lin
-//   phase 3  (DA) per-CTA sums of x_i dA_c and dA_c, Kahan-compensated
+// Inverse z, t stages fused with the pointwise epilogue (FP32 CUDA cores).
+// A 128-thread CTA walks a contiguous range of tiles; a tile is zc z-planes
+// (P = zc * Nt <= 128 points) of one (b, x, y) column and all its channels,
+// one thread per point.
+//   Q[zz][jt][o] = inverse z stage of the column spectrum, with +-k pairing:
+//       Q(z) = sum_{k=0..mz} E_k cos(k th) + i sum_{k=1..mz} O_k sin(k th)
+//       E_0 = U_0, E_k = U_k + U_-k, O_k = U_k - U_-k, E_mz = U_-mz, O_mz = -U_-mz
+//   per point and 4 outputs at a time (shared-memory vector broadcasts):
+//       A_o = bias_o + sum_jt (Qr[jt][o] c_jt(t) - Qi[jt][o] s_jt(t)) + sum_i W(i, o) L_i
+//   SPECTRAL: out = A (no bias, no linear term)   FWD: out = GELU(A)
+//   DA: out = dA = dz GELU'(A), and dW_lin / db partial sums   DX: out = A
 // ---------------------------------------------------------------------------
 struct EpiK {
   EpiArgs a;
-  long long B, Nx, Ny;
-  int Nz, Nt, Jz, Jt, zc;
+  long long NxNy, ntiles;
+  int Nz, Nt, Jz, Jt, mz, zc, P, nzc, CS4;
+  int IB, OB, KG;       // EPI_DA: 4x4 (i, o) blocks of dW_lin, point groups
+  int CLW;              // weight rows held in shared memory (the template's channel bound)
+  uint32_t off[8];      // shared-memory region offsets (16-byte aligned)
 };
 
 static int epi_zc(const Dims& d) {
-  int zc = (int)std::max<int64_t>(1, 256 / d.Nt);
+  int zc = (int)std::max<int64_t>(1, 128 / d.Nt);
   if (zc > d.Nz) zc = (int)d.Nz;
   return zc;
 }
 
-size_t epilogue_smem_bytes(const Dims& d, int mode, int Cs, int Cl) {
+// channel bound of the lin-input register array (template CLM) for Cl channels
+static int epi_clm(int Cl) {
+  if (Cl <= 0) return 0;
+  static const int b[] = {4, 8, 12, 16, 20, 24, 32, 48, 64};
+  for (int v : b)
+    if (Cl <= v) return v;
+  return 64;
+}
+
+static void epi_layout(const Dims& d, int mode, int Cs, int Cl, size_t off[8], size_t& total) {
   const int zc = epi_zc(d);
-  const size_t PP = (size_t)zc * d.Nt + 1;
-  size_t b = sizeof(float2) * (size_t)(Cs * d.Jz * d.Jt + Cs * zc * d.Jt + d.Nz * (d.Jz + 1) +
-                                       d.Jt * d.Nt);
-  b += sizeof(float) * (size_t)(Cl * Cs + Cs);
-  if (mode == EPI_DA) b += sizeof(float) * ((size_t)(Cl + Cs) * PP + 2 * (size_t)(Cl * Cs + Cs));
-  return b;
+  const int P = zc * (int)d.Nt;
+  const int CS4 = (Cs + 3) / 4 * 4;
+  auto al = [](size_t x) { return (x + 15) / 16 * 16; };
+  size_t o = 0;
+  off[0] = o;  // eo: [Cs][Jt][mz+1] float4
+  o = al(o + sizeof(float4) * (size_t)(Cs * d.Jt * (d.mz + 1)));
+  off[1] = o;  // cs: [Nz][mz+1] float2
+  o = al(o + sizeof(float2) * (size_t)(d.Nz * (d.mz + 1)));
+  off[2] = o;  // qs: [zc][Jt][2][CS4] float
+  o = al(o + sizeof(float) * (size_t)(zc * d.Jt * 2 * CS4));
+  off[3] = o;  // w: [CLW][CS4], CLW = Cl rounded up to the kernel's channel bound
+  o = al(o + sizeof(float) * (size_t)(epi_clm(Cl) * CS4));
+  off[4] = o;  // bias: [CS4]
+  o = al(o + sizeof(float) * (size_t)CS4);
+  off[5] = o;  // DA: x tile [Cl][P+1]
+  if (mode == EPI_DA) o = al(o + sizeof(float) * (size_t)(Cl * (P + 1)));
+  off[6] = o;  // DA: dA tile [CS4][P+1]
+  if (mode == EPI_DA) o = al(o + sizeof(float) * (size_t)(CS4 * (P + 1)));
+  off[7] = o;
+  total = o;
+}
+
+size_t epilogue_smem_bytes(const Dims& d, int mode, int Cs, int Cl) {
+  size_t off[8], total;
+  epi_layout(d, mode, Cs, Cl, off, total);
+  if (mode == EPI_DA) {
+    // the final reduction reuses the front of shared memory
+    const int IB = (Cl + 1 + 3) / 4, OB = (Cs + 3) / 4;
+    const size_t red = sizeof(float) * 16 * (size_t)(IB * OB) * (size_t)std::max(1, 128 / (IB * OB));
+    total = std::max(total, red);
+  }
+  return total;
 }
 
 int epilogue_max_grid() { return 1024; }
 
-template <int MODE, int CLM>
-__global__ void __launch_bounds__(256, 2) k_epi_f32(EpiK k) {
+template <int MODE, int CLM, int JTM>
+__global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
   extern __shared__ float4 smem4[];
   const EpiArgs& a = k.a;
-  const int Cs = a.Cs, Cl = a.Cl, Jz = k.Jz, Jt = k.Jt, Nz = k.Nz, Nt = k.Nt, zc = k.zc;
-  const int PP = zc * Nt + 1;
-  float2* sU = reinterpret_cast<float2*>(smem4);  // [Cs][Jz][Jt]
-  float2* sQ = sU + Cs * Jz * Jt;                  // [Cs][zc][Jt]
-  float2* sIz = sQ + Cs * zc * Jt;                 // [Nz][Jz + 1]
-  float2* sIt = sIz + Nz * (Jz + 1);               // [Jt][Nt]
-  float* sW = reinterpret_cast<float*>(sIt + Jt * Nt);  // [Cl][Cs]
-  float* sB = sW + Cl * Cs;                              // [Cs]
-  float* sX = sB + Cs;                                   // DA: [Cl][PP]
-  float* sD = sX + (MODE == EPI_DA ? Cl * PP : 0);       // DA: [Cs][PP]
-  float* sAcc = sD + (MODE == EPI_DA ? Cs * PP : 0);     // DA: sums, then compensations
-  const int npair = Cl * Cs + Cs;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Cs = a.Cs, Cl = (MODE == EPI_SPECTRAL) ? 0 : a.Cl;
+  const int Jz = k.Jz, Jt = k.Jt, Nz = k.Nz, Nt = k.Nt, mz = k.mz, zc = k.zc, P = k.P, CS4 = k.CS4;
+  const int PP = P + 1;
+  unsigned char* base = reinterpret_cast<unsigned char*>(smem4);
+  float4* eo = reinterpret_cast<float4*>(base + k.off[0]);
+  float2* cs = reinterpret_cast<float2*>(base + k.off[1]);
+  float* qs = reinterpret_cast<float*>(base + k.off[2]);
+  float* sw = reinterpret_cast<float*>(base + k.off[3]);
+  float* sbias = reinterpret_cast<float*>(base + k.off[4]);
+  float* sx = reinterpret_cast<float*>(base + k.off[5]);
+  float* sda = reinterpret_cast<float*>(base + k.off[6]);
+  const int tid = threadIdx.x;
 
-  for (int e = tid; e < Nz * Jz; e += nthr) {
-    int r = e / Jz, c = e - r * Jz;
-    sIz[r * (Jz + 1) + c] = a.Iz[e];
+  for (int e = tid; e < Nz * (mz + 1); e += 128) {
+    const int z = e / (mz + 1), kk = e - z * (mz + 1);
+    const float2 f = a.Iz[z * Jz + kk];  // jz = kk: kz = kk (kk < mz), kz = -mz (kk = mz)
+    cs[e] = (kk < mz) ? f : make_float2(f.x, -f.y);
   }
-  for (int e = tid; e < Jt * Nt; e += nthr) sIt[e] = a.It[e];
   if (MODE != EPI_SPECTRAL) {
-    for (int e = tid; e < Cl * Cs; e += nthr) {
-      int i = e / Cs, c = e - i * Cs;
-      sW[e] = a.wlin[(long long)i * a.w_si + (long long)c * a.w_sc];
+    for (int e = tid; e < k.CLW * CS4; e += 128) {
+      const int i = e / CS4, c = e - i * CS4;
+      sw[e] = (c < Cs && i < Cl) ? a.wlin[(long long)i * a.w_si + (long long)c * a.w_sc] : 0.f;
     }
-    for (int c = tid; c < Cs; c += nthr) sB[c] = (MODE == EPI_FWD || MODE == EPI_DA) ? a.bias[c] : 0.f;
   }
-  if (MODE == EPI_DA)
-    for (int e = tid; e < 2 * npair; e += nthr) sAcc[e] = 0.f;
+  for (int c = tid; c < CS4; c += 128)
+    sbias[c] = ((MODE == EPI_FWD || MODE == EPI_DA) && c < Cs) ? a.bias[c] : 0.f;
 
-  const long long NxNy = k.Nx * k.Ny;
+  // this thread's point: t is fixed for the whole kernel
+  const int p = tid;
+  const int t = p % Nt, zz_p = p / Nt;
+  float itr[JTM], iti[JTM];
+#pragma unroll
+  for (int jt = 0; jt < JTM; ++jt) {
+    if (jt < Jt) {
+      const float2 f = a.It[jt * Nt + t];
+      itr[jt] = f.x;
+      iti[jt] = -f.y;
+    } else {
+      itr[jt] = 0.f;
+      iti[jt] = 0.f;
+    }
+  }
+
+  // EPI_DA: this thread's 4x4 block of (i, o) and point group, Kahan running sums
+  const int nblk = k.IB * k.OB;
+  const bool wthread = (MODE == EPI_DA) && tid < nblk * k.KG;
+  const int blk = tid % nblk, kg = tid / nblk;
+  const int i0 = (blk / k.OB) * 4, o0w = (blk % k.OB) * 4;
+  float wsum[16], wcmp[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    wsum[q] = 0.f;
+    wcmp[q] = 0.f;
+  }
+
   const long long plane = (long long)Nz * Nt;
-  const long long chan = NxNy * plane;
-  const long long ncol = k.B * NxNy;
-  const int JZT = Jz * Jt;
-  for (long long col = blockIdx.x; col < ncol; col += gridDim.x) {
-    const long long b = col / NxNy;
-    const long long xy = col - b * NxNy;
-    __syncthreads();
-    for (int e = tid; e < Cs * JZT; e += nthr) {
-      int c = e / JZT, r = e - c * JZT;
-      sU[e] = a.U[((b * Cs + c) * NxNy + xy) * JZT + r];
+  const long long chan = k.NxNy * plane;
+  const long long t_begin = k.ntiles * blockIdx.x / gridDim.x;
+  const long long t_end = k.ntiles * (blockIdx.x + 1) / gridDim.x;
+  long long cur_col = -1;
+  for (long long tau = t_begin; tau < t_end; ++tau) {
+    const long long col = tau / k.nzc;
+    const int z0 = (int)(tau - col * k.nzc) * zc;
+    const int zn = min(zc, Nz - z0);
+    const long long b = col / k.NxNy, xy = col - b * k.NxNy;
+    const int valid = zn * Nt;
+    __syncthreads();  // previous tile's shared-memory reads are done
+    if (col != cur_col) {
+      const int JZT = Jz * Jt;
+      const int neo = Cs * Jt * (mz + 1);
+      for (int e0 = tid; e0 < neo; e0 += 4 * 128) {
+        float2 av[4], mv[4];
+#pragma unroll
+        for (int u4 = 0; u4 < 4; ++u4) {
+          const int e = e0 + u4 * 128;
+          av[u4] = make_float2(0.f, 0.f);
+          mv[u4] = make_float2(0.f, 0.f);
+          if (e < neo) {
+            const int kk = e % (mz + 1), jt = (e / (mz + 1)) % Jt, c = e / ((mz + 1) * Jt);
+            const float2* u = a.U + ((b * Cs + c) * k.NxNy + xy) * JZT + jt;
+            if (kk < mz) av[u4] = __ldg(u + kk * Jt);
+            if (kk > 0) mv[u4] = __ldg(u + (2 * mz - kk) * Jt);
+          }
+        }
+#pragma unroll
+        for (int u4 = 0; u4 < 4; ++u4) {
+          const int e = e0 + u4 * 128;
+          if (e < neo) {
+            const float2 av_ = av[u4], mv_ = mv[u4];
+            eo[e] = make_float4(av_.x + mv_.x, av_.y + mv_.y, av_.x - mv_.x, av_.y - mv_.y);
+          }
+        }
+      }
+      cur_col = col;
+      __syncthreads();
+    }
+    // lin inputs of this point (issued early; consumed after Q is ready)
+    float x[CLM > 0 ? CLM : 1];
+    const long long pofs = xy * plane + (long long)z0 * Nt + p;
+    const bool pv = p < valid;
+    if (MODE != EPI_SPECTRAL) {
+      const float* xp = a.lin_in + (b * Cl) * chan + pofs;
+#pragma unroll
+      for (int i = 0; i < CLM; ++i) x[i] = (i < Cl && pv) ? __ldg(xp + (long long)i * chan) : 0.f;
+    }
+    // Q of this tile's planes: one (o, jt, zz) unit per step
+    {
+      const int units = Cs * Jt * zn;
+      for (int e = tid; e < units; e += 128) {
+        const int zz = e % zn, cj = e / zn;
+        const int jt = cj % Jt, c = cj / Jt;
+        const float4* src = eo + (size_t)(c * Jt + jt) * (mz + 1);
+        const float2* cz = cs + (size_t)(z0 + zz) * (mz + 1);
+        float qr = 0.f, qi = 0.f, qr2 = 0.f, qi2 = 0.f;
+        int kk = 0;
+        for (; kk + 1 <= mz; kk += 2) {
+          const float4 r0 = src[kk], r1 = src[kk + 1];
+          const float2 t0 = cz[kk], t1 = cz[kk + 1];
+          qr = fmaf(r0.x, t0.x, qr);
+          qr = fmaf(-r0.w, t0.y, qr);
+          qi = fmaf(r0.y, t0.x, qi);
+          qi = fmaf(r0.z, t0.y, qi);
+          qr2 = fmaf(r1.x, t1.x, qr2);
+          qr2 = fmaf(-r1.w, t1.y, qr2);
+          qi2 = fmaf(r1.y, t1.x, qi2);
+          qi2 = fmaf(r1.z, t1.y, qi2);
+        }
+        if (kk <= mz) {
+          const float4 r0 = src[kk];
+          const float2 t0 = cz[kk];
+          qr = fmaf(r0.x, t0.x, qr);
+          qr = fmaf(-r0.w, t0.y, qr);
+          qi = fmaf(r0.y, t0.x, qi);
+          qi = fmaf(r0.z, t0.y, qi);
+        }
+        float* qd = qs + ((size_t)(zz * Jt + jt) * 2) * CS4 + c;
+        qd[0] = qr + qr2;
+        qd[CS4] = qi + qi2;
+      }
+      // zero the padded output columns once per tile (read by the vector loads)
+      for (int e = tid; e < zn * Jt * 2 * (CS4 - Cs); e += 128) {
+        const int c = Cs + e % (CS4 - Cs), r = e / (CS4 - Cs);
+        qs[(size_t)r * CS4 + c] = 0.f;
+      }
     }
     __syncthreads();
-    for (int z0 = 0; z0 < Nz; z0 += zc) {
-      const int zn = min(zc, Nz - z0);
-      for (int e = tid; e < Cs * zn * Jt; e += nthr) {
-        int jt = e % Jt;
-        int zz = (e / Jt) % zn;
-        int c = e / (Jt * zn);
-        const float2* iz = sIz + (z0 + zz) * (Jz + 1);
-        const float2* u = sU + c * JZT + jt;
-        float re = 0.f, im = 0.f;
-        for (int jz = 0; jz < Jz; ++jz) {
-          float2 f = iz[jz], v = u[jz * Jt];
-          re = fmaf(f.x, v.x, re);
-          re = fmaf(-f.y, v.y, re);
-          im = fmaf(f.x, v.y, im);
-          im = fmaf(f.y, v.x, im);
-        }
-        sQ[(c * zc + zz) * Jt + jt] = make_float2(re, im);
-      }
-      __syncthreads();
-      for (int pt = tid; pt < zn * Nt; pt += nthr) {
-        const int zz = pt / Nt, t = pt - zz * Nt;
-        const long long pofs = xy * plane + (long long)(z0 + zz) * Nt + t;
-        float L[CLM];
-        if (MODE != EPI_SPECTRAL) {
-#pragma unroll
-          for (int i = 0; i < CLM; ++i)
-            L[i] = (i < Cl) ? a.lin_in[(b * Cl + i) * chan + pofs] : 0.f;
-        }
-        for (int c = 0; c < Cs; ++c) {
-          const float2* q = sQ + (c * zc + zz) * Jt;
-          float sv = 0.f;
-          for (int jt = 0; jt < Jt; ++jt) {
-            float2 qv = q[jt], iv = sIt[jt * Nt + t];
-            sv = fmaf(qv.x, iv.x, sv);
-            sv = fmaf(-qv.y, iv.y, sv);
-          }
-          const long long oofs = (b * Cs + c) * chan + pofs;
-          if (MODE == EPI_SPECTRAL) {
-            a.out[oofs] = sv;
-          } else {
-            float lin = 0.f;
-#pragma unroll
-            for (int i = 0; i < CLM; ++i)
-              if (i < Cl) lin = fmaf(sW[i * Cs + c], L[i], lin);
-            if (MODE == EPI_FWD) {
-              a.out[oofs] = gelu_f(sv + lin + sB[c]);
-            } else if (MODE == EPI_DA) {
-              const float da = a.dz[oofs] * gelu_grad_f(sv + lin + sB[c]);
-              a.out[oofs] = da;
-              sD[c * PP + pt] = da;
-            } else {
-              a.out[oofs] = sv + lin;
-            }
-          }
-        }
+    // per point: 4 outputs at a time (only threads that own a point of this tile)
+    if (pv) {
+      const float* qp = qs + (size_t)(zz_p * Jt) * 2 * CS4;
+      float* optr = a.out + (b * Cs) * chan + pofs;
+      const float* dzp = (MODE == EPI_DA) ? a.dz + (b * Cs) * chan + pofs : nullptr;
+      for (int c0 = 0; c0 < Cs; c0 += 4) {
+        float dzq[4];
         if (MODE == EPI_DA) {
 #pragma unroll
-          for (int i = 0; i < CLM; ++i)
-            if (i < Cl) sX[i * PP + pt] = L[i];
+          for (int q = 0; q < 4; ++q) dzq[q] = (c0 + q < Cs) ? __ldg(dzp + (long long)(c0 + q) * chan) : 0.f;
+        }
+        float4 acc = *reinterpret_cast<const float4*>(sbias + c0);
+#pragma unroll
+        for (int jt = 0; jt < JTM; ++jt) {
+          if (jt < Jt) {
+            const float4 qr = *reinterpret_cast<const float4*>(qp + (size_t)(jt * 2) * CS4 + c0);
+            const float4 qi = *reinterpret_cast<const float4*>(qp + (size_t)(jt * 2 + 1) * CS4 + c0);
+            acc.x = fmaf(qr.x, itr[jt], fmaf(qi.x, iti[jt], acc.x));
+            acc.y = fmaf(qr.y, itr[jt], fmaf(qi.y, iti[jt], acc.y));
+            acc.z = fmaf(qr.z, itr[jt], fmaf(qi.z, iti[jt], acc.z));
+            acc.w = fmaf(qr.w, itr[jt], fmaf(qi.w, iti[jt], acc.w));
+          }
+        }
+        if (MODE != EPI_SPECTRAL) {
+          const float* wp = sw + c0;
+#pragma unroll
+          for (int i = 0; i < CLM; ++i) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wp + (size_t)i * CS4);
+            acc.x = fmaf(w4.x, x[i], acc.x);
+            acc.y = fmaf(w4.y, x[i], acc.y);
+            acc.z = fmaf(w4.z, x[i], acc.z);
+            acc.w = fmaf(w4.w, x[i], acc.w);
+          }
+        }
+        const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = c0 + q;
+          if (c < Cs) {
+            float* o = optr + (long long)c * chan;
+            if (MODE == EPI_FWD) {
+              *o = gelu_f(av[q]);
+            } else if (MODE == EPI_DA) {
+              const float da = dzq[q] * gelu_grad_f(av[q]);
+              *o = da;
+              sda[c * PP + p] = da;
+            } else {
+              *o = av[q];
+            }
+          } else if (MODE == EPI_DA && c < CS4) {
+            sda[c * PP + p] = 0.f;
+          }
         }
       }
+    }
+    if (MODE == EPI_DA) {
+      if (p < P) {
+        if (!pv)
+          for (int c = 0; c < CS4; ++c) sda[c * PP + p] = 0.f;
+#pragma unroll
+        for (int i = 0; i < CLM; ++i)
+          if (i < Cl) sx[i * PP + p] = x[i];
+      }
       __syncthreads();
-      if (MODE == EPI_DA) {
-        const int np = zn * Nt;
-        for (int e = tid; e < npair; e += nthr) {
-          float acc = 0.f;
-          if (e < Cl * Cs) {
-            const int i = e / Cs, c = e - i * Cs;
-            const float* xr = sX + i * PP;
-            const float* dr = sD + c * PP;
-            for (int p = 0; p < np; ++p) acc = fmaf(xr[p], dr[p], acc);
-          } else {
-            const float* dr = sD + (e - Cl * Cs) * PP;
-            for (int p = 0; p < np; ++p) acc += dr[p];
+      if (wthread) {
+        const int pa = kg * P / k.KG, pb = min((kg + 1) * P / k.KG, valid);
+        float part[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) part[q] = 0.f;
+        for (int pt = pa; pt < pb; ++pt) {
+          float xv[4], dv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            xv[u] = i < Cl ? sx[i * PP + pt] : (i == Cl ? 1.f : 0.f);
+            dv[u] = sda[(o0w + u) * PP + pt];
           }
-          // Kahan-compensated running sum over chunks
-          float y = acc - sAcc[npair + e];
-          float t = sAcc[e] + y;
-          sAcc[npair + e] = (t - sAcc[e]) - y;
-          sAcc[e] = t;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) part[u * 4 + v] = fmaf(xv[u], dv[v], part[u * 4 + v]);
         }
-        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float y = part[q] - wcmp[q];
+          const float s = wsum[q] + y;
+          wcmp[q] = (s - wsum[q]) - y;
+          wsum[q] = s;
+        }
       }
     }
   }
   if (MODE == EPI_DA) {
     __syncthreads();
-    for (int e = tid; e < npair; e += nthr)
-      a.part[(long long)blockIdx.x * npair + e] = sAcc[e] - sAcc[npair + e];
+    float* red = reinterpret_cast<float*>(base);
+    if (wthread) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) red[tid * 16 + q] = wsum[q] - wcmp[q];
+    }
+    __syncthreads();
+    const int npair = Cl * Cs + Cs;
+    for (int e = tid; e < nblk * 16; e += 128) {
+      const int bl = e / 16, q = e % 16;
+      const int i = (bl / k.OB) * 4 + q / 4, c = (bl % k.OB) * 4 + q % 4;
+      float s = 0.f, comp = 0.f;
+      for (int g = 0; g < k.KG; ++g) {
+        const float y = red[(g * nblk + bl) * 16 + q] - comp;
+        const float tt = s + y;
+        comp = (tt - s) - y;
+        s = tt;
+      }
+      if (c < Cs && i <= Cl) {
+        const int idx = (i < Cl) ? i * Cs + c : Cl * Cs + c;
+        a.part[(long long)blockIdx.x * npair + idx] = s;
+      }
+    }
   }
 }
 
-template <int MODE, int CLM>
+template <int MODE, int CLM, int JTM>
 static cudaError_t launch_epi_t(const Dims& d, const EpiArgs& a, int* grid_used, cudaStream_t s) {
-  EpiK k;
+  EpiK k{};
   k.a = a;
-  k.B = d.B;
-  k.Nx = d.Nx;
-  k.Ny = d.Ny;
+  k.NxNy = d.Nx * d.Ny;
   k.Nz = (int)d.Nz;
   k.Nt = (int)d.Nt;
   k.Jz = (int)d.Jz;
   k.Jt = (int)d.Jt;
+  k.mz = (int)d.mz;
   k.zc = epi_zc(d);
-  size_t smem = epilogue_smem_bytes(d, MODE, a.Cs, a.Cl);
-  const void* kern = (const void*)k_epi_f32<MODE, CLM>;
+  k.P = k.zc * (int)d.Nt;
+  k.nzc = (int)((d.Nz + k.zc - 1) / k.zc);
+  k.CS4 = (a.Cs + 3) / 4 * 4;
+  const int Cl = MODE == EPI_SPECTRAL ? 0 : a.Cl;
+  k.IB = (Cl + 1 + 3) / 4;
+  k.OB = k.CS4 / 4;
+  k.KG = std::max(1, 128 / (k.IB * k.OB));
+  k.CLW = epi_clm(Cl);
+  k.ntiles = d.B * d.Nx * d.Ny * (long long)k.nzc;
+  {
+    size_t off[8], total;
+    epi_layout(d, MODE, a.Cs, Cl, off, total);
+    for (int q = 0; q < 8; ++q) k.off[q] = (uint32_t)off[q];
+  }
+  const size_t smem = epilogue_smem_bytes(d, MODE, a.Cs, Cl);
+  const void* kern = (const void*)k_epi_f32<MODE, CLM, JTM>;
   cudaError_t e = allow_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  int64_t ncol = d.B * d.Nx * d.Ny;
-  int grid = persistent_grid(kern, 256, smem, ncol);
+  int grid = persistent_grid(kern, 128, smem, k.ntiles);
   if (grid > epilogue_max_grid()) grid = epilogue_max_grid();
   if (grid_used) *grid_used = grid;
   static const char* names[4] = {"fno_epi_spectral_f32", "fno_epi_fwd_f32", "fno_epi_da_f32",
                                  "fno_epi_dx_f32"};
-  FNO_LAUNCH(names[MODE], (k_epi_f32<MODE, CLM>), grid, 256, smem, s, k);
+  FNO_LAUNCH(names[MODE], (k_epi_f32<MODE, CLM, JTM>), grid, 128, smem, s, k);
   return cudaSuccess;
+}
+
+template <int MODE, int JTM>
+static cudaError_t launch_epi_j(const Dims& d, const EpiArgs& a, int* g, cudaStream_t s) {
+  if constexpr (MODE == EPI_SPECTRAL) {
+    return launch_epi_t<MODE, 0, JTM>(d, a, g, s);
+  } else {
+  switch (epi_clm(a.Cl)) {
+    case 4: return launch_epi_t<MODE, 4, JTM>(d, a, g, s);
+    case 8: return launch_epi_t<MODE, 8, JTM>(d, a, g, s);
+    case 12: return launch_epi_t<MODE, 12, JTM>(d, a, g, s);
+    case 16: return launch_epi_t<MODE, 16, JTM>(d, a, g, s);
+    case 20: return launch_epi_t<MODE, 20, JTM>(d, a, g, s);
+    case 24: return launch_epi_t<MODE, 24, JTM>(d, a, g, s);
+    case 32: return launch_epi_t<MODE, 32, JTM>(d, a, g, s);
+    case 48: return launch_epi_t<MODE, 48, JTM>(d, a, g, s);
+    default: return launch_epi_t<MODE, 64, JTM>(d, a, g, s);
+  }
+  }
 }
 
 template <int MODE>
 static cudaError_t launch_epi_m(const Dims& d, const EpiArgs& a, int* g, cudaStream_t s) {
-  if (MODE == EPI_SPECTRAL) return launch_epi_t<MODE, 1>(d, a, g, s);
-  if (a.Cl <= 8) return launch_epi_t<MODE, 8>(d, a, g, s);
-  if (a.Cl <= 16) return launch_epi_t<MODE, 16>(d, a, g, s);
-  if (a.Cl <= 32) return launch_epi_t<MODE, 32>(d, a, g, s);
-  return launch_epi_t<MODE, 64>(d, a, g, s);
+  if (d.Jt <= 8) return launch_epi_j<MODE, 8>(d, a, g, s);
+  return launch_epi_j<MODE, 16>(d, a, g, s);
 }
 
 cudaError_t launch_epilogue_f32(const Dims& d, const EpiArgs& a, int* grid_used, cudaStream_t s) {

@@ -92,13 +92,6 @@ cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const D
                              const float2* ft, const float2* fz, bool split, int* err,
                              cudaStream_t s);
 
-// Inverse z, t and the pointwise epilogue on tcgen05; same contract as
-// launch_epilogue_f32 (EPI_DA writes epilogue_tc_max_grid() partial rows at most).
-bool epilogue_tc_supported(const Dims& d, int mode, int Cs, int Cl, char* why, size_t nwhy);
-cudaError_t launch_epilogue_tc(const Dims& d, const EpiArgs& a, bool split, int* err,
-                               int* grid_used, cudaStream_t s);
-int epilogue_tc_max_grid();
-
 #ifdef __CUDACC__
 __device__ __forceinline__ float gelu_f(float a) {
   return 0.5f * a * (1.0f + erff(a * 0.70710678118654752440f));
