@@ -11,6 +11,11 @@ B*C_in*Nx*Ny*Nz*Nt per step / step time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl ours|reference]
 
+The headline precision is split BF16 (bf16x3: DFT contractions on the tensor
+cores as hi.hi + hi.lo + lo.hi products, FP32 accumulation).  After the timed
+region the same inputs are run in FP32 (plain form) and BF16 as well; the line
+carries their step times and the rel-L2 of every result against FP32.
+
 --impl reference times the FP64 CPU oracle (the baseline arm) on a bounded
 sample of the same workload (fewer channels), on the host cores.
 """
@@ -138,6 +143,75 @@ def algorithmic(name, d):
     return None, None
 
 
+def alu_peak_tflops(pk):
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x maximum SM clock."""
+    return 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+
+
+def roofline_of(name, per_launch_ms, dd, pk, precision):
+    """Roofline entry of one kernel: the bound (hbm, alu or tensor) with the larger fraction."""
+    nbytes, nflops = algorithmic(name, dd)
+    if nbytes is None:
+        return None
+    sec = per_launch_ms * 1e-3
+    gbs = nbytes / sec / 1e9
+    tfl = nflops / sec / 1e12
+    f_hbm = gbs / pk["hbm_gbs"]
+    if "_tc" in name:
+        # split BF16 issues three products per real multiply-add
+        tf_issued = tfl * (3 if name.endswith("bf16x3") else 1)
+        comp = {"bound": "tensor", "achieved": round(tf_issued, 2), "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": round(tf_issued / pk["bf16_tflops"], 4),
+                "peak_src": pk["src"] + " cuBLAS bf16 burst"}
+    else:
+        ap = alu_peak_tflops(pk)
+        comp = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(ap, 1), "unit": "TFLOP/s",
+                "frac": round(tfl / ap, 4),
+                "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x max SM clock"}
+    hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": round(f_hbm, 4), "peak_src": pk["src"] + " copy bandwidth"}
+    best, other = (hbm, comp) if f_hbm >= comp["frac"] else (comp, hbm)
+    out = dict(best)
+    out.update({"traffic": None, "kernel": name, "ms_per_launch": round(per_launch_ms, 4),
+                "alg_bytes": nbytes, "alg_flops": nflops,
+                "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+    return out
+
+
+def precision_sweep(args, step_of, outs, stream, barrier, units):
+    """Time the other precisions on the resident inputs; rel-L2 of every result vs FP32."""
+    import torch
+    ref_prec = "fp32"
+    runs = {}
+    ref = None
+    for prec in ["fp32", "bf16", "bf16x3"]:
+        st = step_of(prec)
+        for _ in range(3):
+            st()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            st()
+        b.record(stream)
+        barrier()
+        ms = a.elapsed_time(b) / args.steps
+        res = [t.detach().double().clone() if prec == ref_prec else t.detach().double() for t in outs]
+        if prec == ref_prec:
+            ref = res
+            err = None
+        else:
+            err = {k: float(torch.linalg.vector_norm(r - q) / torch.linalg.vector_norm(q))
+                   for k, r, q in zip(("z", "dx", "dw", "dw_lin", "db"), res, ref)}
+        runs[prec] = {"ms_per_step": round(ms, 3), "value": units / (ms * 1e-3) / 1e9,
+                      "rel_l2_vs_fp32": err}
+        del res
+    runs["note"] = ("FP32 plain form vs the FP64 oracle: rel-L2 ~1e-7 in the parity tests; "
+                    "tolerances vs the oracle: fp32 and bf16x3 1e-5, bf16 2e-2")
+    return runs
+
+
 def oracle_sample_time(wl_name, sample_channels, seed=1000):
     """Seconds of one oracle fwd+bwd on the workload grid with fewer channels, and its units."""
     import numpy as np
@@ -195,10 +269,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -241,17 +316,24 @@ def main():
     db = torch.empty_like(bias)
     d = ops.dims_of(x, C, modes)
     p = ops.precision_code(args.precision)
-    nws = max(_lib.fno_workspace_bytes(d, p, ops.OP_BLOCK_FWD), _lib.fno_workspace_bytes(d, p, ops.OP_BLOCK_BWD))
+    nws = max(_lib.fno_workspace_bytes(d, ops.precision_code(q), op)
+              for q in ("fp32", "bf16", "bf16x3") for op in (ops.OP_BLOCK_FWD, ops.OP_BLOCK_BWD))
     ws = torch.empty(nws, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = int(stream.cuda_stream)
 
-    def step():
-        _lib.fno_block_fwd(d, p, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
-                           z.data_ptr(), ws.data_ptr(), nws, sh)
-        _lib.fno_block_bwd(d, p, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
-                           dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(),
-                           db.data_ptr(), ws.data_ptr(), nws, sh)
+    def step_of(prec):
+        pc = ops.precision_code(prec)
+
+        def st():
+            _lib.fno_block_fwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                               z.data_ptr(), ws.data_ptr(), nws, sh)
+            _lib.fno_block_bwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                               dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(),
+                               db.data_ptr(), ws.data_ptr(), nws, sh)
+        return st
+
+    step = step_of(args.precision)
 
     def barrier():
         if dist is not None:
@@ -318,35 +400,20 @@ def main():
     pk = peaks()
     dd = {"B": B, "Ci": C, "Co": C, "Nx": Nx, "Ny": Ny, "Nz": Nz, "Nt": Nt,
           "Jx": 2 * mx, "Jy": 2 * my, "Jz": 2 * mz, "Jt": mt}
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
-    roof = None
     kernel_share = {}
     tot_prof = sum(v[1] for v in prof.values()) if prof else 0.0
-    for k, (n, t) in prof.items():
-        kernel_share[k] = {"launches": n, "ms": round(t, 4), "share": round(t / tot_prof, 4) if tot_prof else None}
-    if top is not None:
-        name, (n, t) = top
-        per_launch_ms = t / n
-        nbytes, nflops = algorithmic(name, dd)
-        if nbytes is not None:
-            gbs = nbytes / (per_launch_ms * 1e-3) / 1e9
-            tfl = nflops / (per_launch_ms * 1e-3) / 1e12
-            if args.precision == "fp32":
-                alu_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-                f_hbm, f_alu = gbs / pk["hbm_gbs"], tfl / alu_peak
-                if f_alu >= f_hbm:
-                    roof = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(alu_peak, 1),
-                            "unit": "TFLOP/s", "frac": round(f_alu, 4), "traffic": None,
-                            "kernel": name, "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock",
-                            "hbm_frac": round(f_hbm, 4)}
-                else:
-                    roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
-                            "unit": "GB/s", "frac": round(f_hbm, 4), "traffic": None,
-                            "kernel": name, "peak_src": pk["src"], "alu_frac": round(f_alu, 4)}
-            else:
-                roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
-                        "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 4), "traffic": None,
-                        "kernel": name, "peak_src": pk["src"]}
+    for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        r = roofline_of(k, t / n, dd, pk, args.precision)
+        kernel_share[k] = {"launches": n, "ms": round(t, 4),
+                           "share": round(t / tot_prof, 4) if tot_prof else None,
+                           "bound": r["bound"] if r else None, "frac": r["frac"] if r else None}
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = roofline_of(top[0], top[1][1] / top[1][0], dd, pk, args.precision) if top else None
+
+    # ---- the other precisions on the same inputs: time and error vs the FP32 plain form ----
+    sweep = None
+    if not args.no_sweep:
+        sweep = precision_sweep(args, step_of, (z, dx, dw, dwl, db), stream, barrier, units * world)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -360,7 +427,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32",
                                            "bf16x3": "bf16x3+f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "B": B, "C_in": C, "C_out": C,
@@ -369,7 +436,7 @@ def main():
                        "l2": "inputs larger than L2 (5.4 GB per tensor); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "kernels": kernel_share,
+            "clocks": clocks, "kernels": kernel_share, "precision_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -23,6 +23,7 @@ dot-products and central finite differences).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -41,17 +42,23 @@ _F64P = ctypes.POINTER(ctypes.c_double)
 _I64P = ctypes.POINTER(ctypes.c_int64)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (portable flags, no -march)."""
+def build(force: bool = False, mutant: int = 0) -> str:
+    """Compile the oracle with the host C compiler (portable flags, no -march).
+
+    ``mutant`` > 0 builds a copy with one planted slip (see ORACLE_MUTANT in
+    fno_oracle.c); only the mutation tests ask for one.
+    """
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    so = _SO if mutant == 0 else os.path.join(_OUT_DIR, f"liboracle_mutant{int(mutant)}.so")
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(_SRC)):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+           f"-DORACLE_MUTANT={int(mutant)}", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
 def _load():
@@ -59,37 +66,55 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
-        vp = ctypes.c_void_p
-        i64 = ctypes.c_int64
-        ci = ctypes.c_int
-        lib.oracle_threads.argtypes = [ci]
-        lib.oracle_threads.restype = ci
-        lib.oracle_gelu.argtypes = [ctypes.c_double]
-        lib.oracle_gelu.restype = ctypes.c_double
-        lib.oracle_gelu_grad.argtypes = [ctypes.c_double]
-        lib.oracle_gelu_grad.restype = ctypes.c_double
-        for name in ("oracle_spectrum", "oracle_spectrum_bruteforce"):
-            fn = getattr(lib, name)
-            fn.argtypes = [_I64P, i64, vp, vp, ci]
-            fn.restype = ci
-        for name in ("oracle_synthesis", "oracle_synthesis_bruteforce"):
-            fn = getattr(lib, name)
-            fn.argtypes = [_I64P, i64, vp, vp, ci]
-            fn.restype = ci
-        lib.oracle_synthesis_points.argtypes = [_I64P, i64, vp, i64, vp, vp, ci]
-        lib.oracle_synthesis_points.restype = ci
-        lib.oracle_mix.argtypes = [_I64P, vp, vp, vp]
-        lib.oracle_mix.restype = ci
-        lib.oracle_mix_adjoint.argtypes = [_I64P, vp, vp, vp, vp, vp]
-        lib.oracle_mix_adjoint.restype = ci
-        lib.oracle_block_fwd.argtypes = [_I64P, ci, ci, vp, vp, vp, vp, vp, i64, vp, vp]
-        lib.oracle_block_fwd.restype = ci
-        lib.oracle_block_bwd.argtypes = [_I64P, ci, ci, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp,
-                                         vp, vp]
-        lib.oracle_block_bwd.restype = ci
+        _lib = _bind(ctypes.CDLL(build()))
+        return _lib
+
+
+@contextlib.contextmanager
+def mutant(k: int):
+    """Run the enclosed calls on a build with planted slip k (mutation tests only)."""
+    global _lib
+    lib = _bind(ctypes.CDLL(build(mutant=k)))
+    with _lock:
+        old = _lib
         _lib = lib
-        return lib
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = old
+
+
+def _bind(lib):
+    vp = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    ci = ctypes.c_int
+    lib.oracle_threads.argtypes = [ci]
+    lib.oracle_threads.restype = ci
+    lib.oracle_gelu.argtypes = [ctypes.c_double]
+    lib.oracle_gelu.restype = ctypes.c_double
+    lib.oracle_gelu_grad.argtypes = [ctypes.c_double]
+    lib.oracle_gelu_grad.restype = ctypes.c_double
+    for name in ("oracle_spectrum", "oracle_spectrum_bruteforce"):
+        fn = getattr(lib, name)
+        fn.argtypes = [_I64P, i64, vp, vp, ci]
+        fn.restype = ci
+    for name in ("oracle_synthesis", "oracle_synthesis_bruteforce"):
+        fn = getattr(lib, name)
+        fn.argtypes = [_I64P, i64, vp, vp, ci]
+        fn.restype = ci
+    lib.oracle_synthesis_points.argtypes = [_I64P, i64, vp, i64, vp, vp, ci]
+    lib.oracle_synthesis_points.restype = ci
+    lib.oracle_mix.argtypes = [_I64P, vp, vp, vp]
+    lib.oracle_mix.restype = ci
+    lib.oracle_mix_adjoint.argtypes = [_I64P, vp, vp, vp, vp, vp]
+    lib.oracle_mix_adjoint.restype = ci
+    lib.oracle_block_fwd.argtypes = [_I64P, ci, ci, vp, vp, vp, vp, vp, i64, vp, vp]
+    lib.oracle_block_fwd.restype = ci
+    lib.oracle_block_bwd.argtypes = [_I64P, ci, ci, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp,
+                                     vp, vp]
+    lib.oracle_block_bwd.restype = ci
+    return lib
 
 
 class Dims:

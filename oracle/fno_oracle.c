@@ -50,6 +50,16 @@
 
 #define TWO_PI 6.283185307179586476925286766559005768
 
+/* Mutation hooks for the pin tests: a test build defines ORACLE_MUTANT = k to
+ * plant one known slip (1 stored-index map off by one, 2 dropped c(kt),
+ * 3 wrong sign of the t exponent, 4 missing 1/N, 5 transposed W_l in the
+ * forward, 6 conjugate dropped in dW, 7 GELU' without its second term) and
+ * checks that some pin fails.  The oracle itself is built with 0. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+#define MUT(k) (ORACLE_MUTANT == (k))
+
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
 
 typedef struct {
@@ -81,10 +91,11 @@ static int64_t rmod(int64_t a, int64_t n) {
 }
 
 /* signed frequency of stored index j on a symmetric axis with m kept per side */
-static int64_t kfreq(int64_t j, int64_t m) { return j < m ? j : j - 2 * m; }
+static int64_t kfreq(int64_t j, int64_t m) { return j < m ? j : j - 2 * m + (MUT(1) ? 1 : 0); }
 
 /* weight of a half-spectrum bin in the real synthesis */
 static double cweight(int64_t kt, int64_t Nt) {
+  if (MUT(2)) return 1.0;
   if (kt == 0) return 1.0;
   if (Nt % 2 == 0 && 2 * kt == Nt) return 1.0;
   return 2.0;
@@ -231,7 +242,7 @@ static void spectrum_one(const dims_t* d, const tables_t* T, const double* f, do
       for (int64_t t = 0; t < Nt; ++t) {
         int64_t q = rmod(T->kt[jt] * t, Nt);
         re += src[t] * T->t.c[q];
-        im -= src[t] * T->t.s[q];
+        im -= (MUT(3) ? -1.0 : 1.0) * src[t] * T->t.s[q];
       }
       dst[2 * jt] = re;
       dst[2 * jt + 1] = im;
@@ -261,7 +272,7 @@ static void synthesis_one(const dims_t* d, const tables_t* T, const double* fh, 
   axis_inverse(w->p3, w->p2, d->Nx, d->Jy, d->Ny, d->Jz * Jt, T->ky, &T->y);
   axis_inverse(w->p2, w->p1, d->Nx * d->Ny, d->Jz, d->Nz, Jt, T->kz, &T->z);
   const int64_t rows = d->Nx * d->Ny * d->Nz;
-  const double invN = 1.0 / (double)d->Ng;
+  const double invN = MUT(4) ? 1.0 : 1.0 / (double)d->Ng;
   const double* q1 = w->p1;
 #pragma omp parallel for schedule(static)
   for (int64_t r = 0; r < rows; ++r) {
@@ -313,6 +324,7 @@ static double synthesis_point(const dims_t* d, const tables_t* T, const double* 
 static double gelu(double a) { return 0.5 * a * (1.0 + erf(a / sqrt(2.0))); }
 
 static double gelu_grad(double a) {
+  if (MUT(7)) return 0.5 * (1.0 + erf(a / sqrt(2.0)));
   return 0.5 * (1.0 + erf(a / sqrt(2.0))) + a * exp(-0.5 * a * a) / sqrt(TWO_PI);
 }
 
@@ -477,7 +489,7 @@ static void mix_adjoint(const dims_t* d, const double* xh, const void* w, int wt
           const double* a = xh + 2 * ((b * d->Ci + i) * Mk);
           const double* gg = g + 2 * ((b * d->Co + o) * Mk);
           for (int64_t j = 0; j < Mk; ++j) {
-            double ar = a[2 * j], ai = -a[2 * j + 1];
+            double ar = a[2 * j], ai = (MUT(6) ? 1.0 : -1.0) * a[2 * j + 1];
             dst[2 * j] += ar * gg[2 * j] - ai * gg[2 * j + 1];
             dst[2 * j + 1] += ar * gg[2 * j + 1] + ai * gg[2 * j];
           }
@@ -536,7 +548,8 @@ static double pre_activation(const dims_t* d, const void* x, const void* wl, con
                              int dtype, int64_t b, int64_t o, int64_t p, double s) {
   double a = s + ld(bias, dtype, o);
   for (int64_t i = 0; i < d->Ci; ++i)
-    a += ld(x, dtype, (b * d->Ci + i) * d->Ng + p) * ld(wl, dtype, i * d->Co + o);
+    a += ld(x, dtype, (b * d->Ci + i) * d->Ng + p) *
+         ld(wl, dtype, MUT(5) ? o * d->Ci + i : i * d->Co + o);
   return a;
 }
 

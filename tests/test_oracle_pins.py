@@ -368,3 +368,44 @@ def test_gelu_textbook_values():
         h = 1e-5
         fd = (oracle.gelu(a + h) - oracle.gelu(a - h)) / (2 * h)
         assert abs(fd - oracle.gelu_grad(a)) < 1e-9
+
+
+# ------------------------------------------------------- linearity, bypass
+
+def test_spectral_part_is_linear_in_x_and_in_w():
+    d = Dims(2, 3, 2, 6, 5, 4, 6, 2, 2, 1, 3)
+    g = rng(70)
+    x1, x2 = (g.standard_normal((d.B, d.Ci) + d.grid) for _ in range(2))
+    w1, w2 = w_real(rand_w(d, 71)), w_real(rand_w(d, 72))
+    a, b = 0.7, -1.9
+    s1, _ = oracle.block_fwd(d, x1, w1)
+    s2, _ = oracle.block_fwd(d, x2, w1)
+    s12, _ = oracle.block_fwd(d, a * x1 + b * x2, w1)
+    assert relerr(s12, a * s1 + b * s2) < 1e-12
+    t2, _ = oracle.block_fwd(d, x1, w2)
+    t12, _ = oracle.block_fwd(d, x1, a * w1 + b * w2)
+    assert relerr(t12, a * s1 + b * t2) < 1e-12
+
+
+def test_zero_spectral_weight_reduces_to_torch_linear_gelu():
+    # With W = 0 the block is a dense 1x1 layer with exact GELU; PyTorch's CPU
+    # FP64 linear + gelu (erf form) and autograd give its value and gradients.
+    torch = pytest.importorskip("torch")
+    d = Dims(2, 3, 5, 4, 3, 5, 6, 1, 1, 2, 2)
+    g = rng(80)
+    x = g.standard_normal((d.B, d.Ci) + d.grid)
+    wl = g.uniform(-1, 1, (d.Ci, d.Co))
+    b = g.uniform(-1, 1, d.Co)
+    dz = g.standard_normal((d.B, d.Co) + d.grid)
+    w0 = np.zeros((d.Ci, d.Co) + d.modes + (2,))
+    z, _ = oracle.block_fwd(d, x, w0, wl, b)
+    gr = oracle.block_bwd(d, x, w0, dz, wl, b)
+    X = torch.tensor(np.moveaxis(x, 1, -1), dtype=torch.float64, requires_grad=True)
+    WL = torch.tensor(wl.T.copy(), dtype=torch.float64, requires_grad=True)   # nn.Linear: [out][in]
+    Bb = torch.tensor(b, dtype=torch.float64, requires_grad=True)
+    Z = torch.nn.functional.gelu(torch.nn.functional.linear(X, WL, Bb), approximate="none")
+    Z.backward(torch.tensor(np.moveaxis(dz, 1, -1)))
+    assert relerr(z, np.moveaxis(Z.detach().numpy(), -1, 1)) < 1e-13
+    assert relerr(gr["dx"], np.moveaxis(X.grad.numpy(), -1, 1)) < 1e-12
+    assert relerr(gr["dwl"], WL.grad.numpy().T) < 1e-12
+    assert relerr(gr["db"], Bb.grad.numpy()) < 1e-12
