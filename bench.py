@@ -137,10 +137,21 @@ def algorithmic(name, d):
     if name.startswith("fno_epi_fwd"):
         return 2 * grid + t1, f_inv + f_lin
     if name.startswith("fno_epi_da"):
-        return 4 * grid + t1, f_inv + 2 * f_lin
+        return 3 * grid + t1, f_inv + 2 * f_lin
     if name.startswith("fno_epi_dx"):
         return 2 * grid + t1, f_inv + f_lin
     return None, None
+
+
+# DRAM bytes per launch per point-channel (B*C_in*N) from one ncu capture of the
+# kernel at ns_block_64c_t16 (dram__bytes_read.sum + dram__bytes_write.sum),
+# which scales in proportion to the units processed.  An entry is removed when
+# its kernel changes.
+TRAFFIC_PER_UNIT = {
+    "fno_epi_fwd_f32": (0.805e9 + 0.6312e9) / 167772160,
+    "fno_epi_da_f32": (1.476e9 + 0.646e9) / 167772160,
+    "fno_epi_dx_f32": (0.8049e9 + 0.6129e9) / 167772160,
+}
 
 
 def alu_peak_tflops(pk):
@@ -172,7 +183,11 @@ def roofline_of(name, per_launch_ms, dd, pk, precision):
            "frac": round(f_hbm, 4), "peak_src": pk["src"] + " copy bandwidth"}
     best, other = (hbm, comp) if f_hbm >= comp["frac"] else (comp, hbm)
     out = dict(best)
-    out.update({"traffic": None, "kernel": name, "ms_per_launch": round(per_launch_ms, 4),
+    tpu = TRAFFIC_PER_UNIT.get(name)
+    units = dd["B"] * dd["Ci"] * dd["Nx"] * dd["Ny"] * dd["Nz"] * dd["Nt"]
+    out.update({"traffic": round(tpu * units) if tpu else None,
+                "traffic_src": "ncu dram bytes at ns_block_64c_t16, scaled by units" if tpu else None,
+                "kernel": name, "ms_per_launch": round(per_launch_ms, 4),
                 "alg_bytes": nbytes, "alg_flops": nflops,
                 "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
     return out

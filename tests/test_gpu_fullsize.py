@@ -1,0 +1,98 @@
+"""Full-size parity on the benchmark workload, on sampled outputs.
+
+The CO2-like block: B = 1, width 20, grid 128 x 128 x 128 x 32 (2.1 M cells x
+32 steps), kept modes 12/12/8/8, input the same seeded anisotropic Gaussian
+random field that bench.py times (correlation 20 x 20 x 4 cells, 8 steps),
+upstream gradient N(0, 1).  The GPU runs fno_block_fwd + fno_block_bwd through
+the C ABI with one workspace, as the benchmark does.  The FP64 oracle computes
+the full kept spectra (Alg. 2) and evaluates Z and dX at 96 sampled grid points
+(corners and edges of every axis included); dW, dW_lin and db are compared in
+full.  Tolerance: rel-L2 per tensor, FP32 and split BF16 <= 1e-5, BF16 <= 2e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Dims
+from paper_2211_12709_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-2}
+D = Dims(1, 20, 20, 128, 128, 128, 32, 12, 12, 8, 8)
+ELL = (20.0, 20.0, 4.0, 8.0)
+CFG = 4
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def sample_points(d, n, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    pts = np.stack([g.integers(0, s, n) for s in d.grid], axis=1)
+    edges = []
+    for a, s in enumerate(d.grid):
+        for v in (0, s - 1):
+            p = [s2 // 2 for s2 in d.grid]
+            p[a] = v
+            edges.append(p)
+    edges.append([0, 0, 0, 0])
+    edges.append([s - 1 for s in d.grid])
+    return np.concatenate([np.array(edges, dtype=np.int64), pts.astype(np.int64)])[:96]
+
+
+@pytest.fixture(scope="module")
+def case():
+    d = D
+    x = inputs.grf((d.B, d.Ci), d.grid, ELL, inputs.SEED_INPUT + CFG)
+    w = inputs.spectral_weights(d.Ci, d.Co, d.modes, inputs.SEED_SPECTRAL_W + CFG)
+    wl, b = inputs.linear_params(d.Ci, d.Co, inputs.SEED_LINEAR + CFG)
+    dz = inputs.normal((d.B, d.Co) + d.grid, inputs.SEED_UPSTREAM + CFG)
+    pts = sample_points(d, 96, 77)
+    _, zp = oracle.block_fwd(d, x, w, wl, b, full=False, pts=pts)
+    ref = oracle.block_bwd(d, x, w, dz, wl, b, full=False, pts=pts)
+    ref["z_pts"] = zp
+    return d, x, w, wl, b, dz, pts, ref
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp32", "bf16"])
+def test_block_fwd_bwd_full_size_sampled(case, precision):
+    from paper_2211_12709_gb300 import _lib, ops
+    d, x, w, wl, b, dz, pts, ref = case
+    dev = torch.device("cuda", 0)
+    X = torch.from_numpy(x).to(dev)
+    DZ = torch.from_numpy(dz).to(dev)
+    W = torch.from_numpy(w).to(dev)
+    WL = torch.from_numpy(wl).to(dev)
+    Bb = torch.from_numpy(b).to(dev)
+    Z = torch.empty_like(X)
+    DX = torch.empty_like(X)
+    DW = torch.empty_like(W)
+    DWL = torch.empty_like(WL)
+    DB = torch.empty_like(Bb)
+    dims = ops.dims_of(X, d.Co, (d.mx, d.my, d.mz, d.mt))
+    p = ops.precision_code(precision)
+    nws = max(_lib.fno_workspace_bytes(dims, p, ops.OP_BLOCK_FWD),
+              _lib.fno_workspace_bytes(dims, p, ops.OP_BLOCK_BWD))
+    ws = torch.empty(nws, dtype=torch.uint8, device=dev)
+    sh = int(torch.cuda.current_stream(dev).cuda_stream)
+    _lib.fno_block_fwd(dims, p, X.data_ptr(), W.data_ptr(), WL.data_ptr(), Bb.data_ptr(),
+                       Z.data_ptr(), ws.data_ptr(), nws, sh)
+    _lib.fno_block_bwd(dims, p, X.data_ptr(), W.data_ptr(), WL.data_ptr(), Bb.data_ptr(),
+                       DZ.data_ptr(), DX.data_ptr(), DW.data_ptr(), DWL.data_ptr(), DB.data_ptr(),
+                       ws.data_ptr(), nws, sh)
+    _lib.fno_workspace_status(ws.data_ptr(), sh)
+    torch.cuda.synchronize()
+    ix = [torch.from_numpy(pts[:, a]).to(dev) for a in range(4)]
+    z_pts = Z[:, :, ix[0], ix[1], ix[2], ix[3]].cpu().numpy()
+    dx_pts = DX[:, :, ix[0], ix[1], ix[2], ix[3]].cpu().numpy()
+    errs = {"z": relerr(z_pts, ref["z_pts"]), "dx": relerr(dx_pts, ref["dx_pts"]),
+            "dw": relerr(DW.cpu().numpy(), ref["dw"]), "dwl": relerr(DWL.cpu().numpy(), ref["dwl"]),
+            "db": relerr(DB.cpu().numpy(), ref["db"])}
+    print("128^3x32 width 20", precision, errs)
+    assert all(np.isfinite(v) and v <= TOL[precision] for v in errs.values()), errs
