@@ -157,7 +157,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t err;  // device status word (nonzero: a bounded wait gave up)
   size_t tab[10];
-  size_t t1, t2, xh, yh, gxh, da, part, total;
+  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, total;
   bool da_in_dx;
 };
 
@@ -196,6 +196,8 @@ static Layout layout(const Dims& d, int op) {
     const int rows = epilogue_max_grid();
     off += align256(sizeof(float) * (size_t)rows * (size_t)(d.Ci * d.Co + d.Co));
   }
+  L.mma_tab = off;  // basis fragments of the mma.sync epilogue
+  off += align256(epilogue_mma_table_bytes(d));
   L.total = off;
   return L;
 }
@@ -253,12 +255,13 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
   return FNO_OK;
 }
 
-// The fused inverse z, t + epilogue stage runs in FP32 on the CUDA cores for
-// every precision (see fno_tc.cu for the measured reason).
-static cudaError_t epilogue(const Dims& d, const EpiArgs& a, int precision, int* err, int* grid_used,
-                            cudaStream_t s) {
-  (void)precision;
-  (void)err;
+// The fused inverse z, t + epilogue stage: warp-level mma.sync (BF16 or split
+// BF16) for the tensor-core precisions where its tiling applies, else FP32 on
+// the CUDA cores (the plain form, and the exact fallback for other shapes).
+static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base, const Layout& L,
+                            int* err, int* grid_used, cudaStream_t s) {
+  if (is_tc(precision) && epilogue_mma_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
+    return launch_epilogue_mma(d, a, precision == FNO_BF16X3, base + L.mma_tab, err, grid_used, s);
   return launch_epilogue_f32(d, a, grid_used, s);
 }
 
@@ -301,7 +304,7 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   a.Cl = (op == FNO_OP_BLOCK_FWD) ? (int)d.Ci : 0;
   a.w_si = (int)d.Co;
   a.w_sc = 1;
-  CK(epilogue(d, a, precision, err, nullptr, s));
+  CK(epilogue(d, a, precision, base, L, err, nullptr, s));
   return FNO_OK;
 }
 
@@ -382,7 +385,7 @@ int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const 
     a.It = T.Itu;
     a.Cs = (int)d.Ci;
     a.Cl = 0;
-    CK(epilogue(d, a, precision, err, nullptr, s));
+    CK(epilogue(d, a, precision, base, L, err, nullptr, s));
   }
   return FNO_OK;
 }
@@ -447,7 +450,7 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   a.w_si = (int)d.Co;
   a.w_sc = 1;
   int rows = 0;
-  CK(epilogue(d, a, precision, err, &rows, s));
+  CK(epilogue(d, a, precision, base, L, err, &rows, s));
   CK(launch_reduce_partials(part, rows, (int)d.Ci, (int)d.Co, dw_lin, db, s));
   // G = (c/N) DFT(dA); dW and the input-spectrum gradient
   if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s, precision, err))) return rc;
@@ -466,7 +469,7 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   q.Cl = (int)d.Co;
   q.w_si = 1;
   q.w_sc = (int)d.Co;
-  CK(epilogue(d, q, precision, err, nullptr, s));
+  CK(epilogue(d, q, precision, base, L, err, nullptr, s));
   return FNO_OK;
 }
 

@@ -17,14 +17,6 @@
 
 namespace fno {
 
-#define FNO_LAUNCH(name, kern, grid, block, smem, stream, ...)   \
-  do {                                                           \
-    prof_before(name, stream);                                   \
-    kern<<<grid, block, smem, stream>>>(__VA_ARGS__);            \
-    cudaError_t e_ = cudaGetLastError();                         \
-    prof_after(stream);                                          \
-    if (e_ != cudaSuccess) return e_;                            \
-  } while (0)
 
 static int persistent_grid(const void* kern, int threads, size_t smem, int64_t work) {
   int per_sm = 0;

@@ -84,6 +84,14 @@ cudaError_t launch_reduce_partials(const float* part, int rows, int Ci, int Co, 
 
 cudaError_t launch_fill_zero(float* p, int64_t n, cudaStream_t s);
 
+// Inverse z, t + epilogue on warp-level mma.sync (fno_mma.cu), BF16 or split
+// BF16; same contract as launch_epilogue_f32.  table: device scratch of
+// epilogue_mma_table_bytes(d) for the basis fragments.
+bool epilogue_mma_supported(const Dims& d, int mode, int Cs, int Cl, char* why, size_t nwhy);
+size_t epilogue_mma_table_bytes(const Dims& d);
+cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, void* table, int* err,
+                                int* grid_used, cudaStream_t s);
+
 // ---- tensor-core path (fno_tc.cu) -------------------------------------------
 // Pruned DFT over t then z on tcgen05 (BF16 or split BF16); same contract as
 // launch_fwd_tz_f32.  err: device word set to nonzero when a bounded wait gives up.
@@ -93,6 +101,15 @@ cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const D
                              cudaStream_t s);
 
 #ifdef __CUDACC__
+// Launch with the profiling hooks; returns the launch error from the caller.
+#define FNO_LAUNCH(name, kern, grid, block, smem, stream, ...)   \
+  do {                                                           \
+    prof_before(name, stream);                                   \
+    kern<<<grid, block, smem, stream>>>(__VA_ARGS__);            \
+    cudaError_t e_ = cudaGetLastError();                         \
+    prof_after(stream);                                          \
+    if (e_ != cudaSuccess) return e_;                            \
+  } while (0)
 __device__ __forceinline__ float gelu_f(float a) {
   return 0.5f * a * (1.0f + erff(a * 0.70710678118654752440f));
 }

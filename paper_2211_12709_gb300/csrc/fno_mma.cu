@@ -1,0 +1,835 @@
+// fno_mma.cu -- inverse z, t stages fused with the pointwise epilogue on the
+// tensor cores through warp-level mma.sync (BF16 or split BF16, FP32
+// accumulation): the last stage of the inverse transform of Alg. 2 (Sec. IV-C)
+// with the 1x1 bypass, bias and GELU of the block, and in its dA mode the
+// dW_lin / db reductions of the backward pass.
+//
+// Why mma.sync and not tcgen05 here: the contractions of this stage are skinny
+// (N = output channels <= 32, K <= 48).  One tcgen05.mma with M = 128, K = 16
+// costs about 153 SM cycles whatever its N, so at N = 24 it delivers about
+// 320 MAC/clk/SM; mma.sync m16n8k16 sustains about 965 MAC/clk/SM on this GPU
+// (FP32 FFMA: 117), keeps operands and accumulators in registers, and feeds
+// the GELU epilogue without a TMEM round trip.
+//
+// A tile is 128 points of one (b, x, y) column: ZB = 128 / Nt z-planes.  Each
+// of the 8 warps owns one m-tile of 16 consecutive points.  Per tile:
+//   stage 1 (inverse z, complex, as a real GEMM)
+//     Q[(o, jt)][(z, re/im)] = sum_k U'[(o, jt)][k] Bz[k][(z, re/im)],
+//     k = (jz, re/im); A = U' (the column's spectrum in shared memory, rebuilt
+//     when the column changes), B = basis fragments from a global table.
+//   stage 2 (inverse t) + stage 3 (1x1):
+//     acc[p = (z, t)][o] = bias[o] + sum_k2 Tb[t][k2] Q[z][o][k2]
+//                                  + sum_i  X[i][p] Wl[i][o]
+//     k2 = (re/im, jt); Tb holds c(kt)/N cos and -c(kt)/N sin.
+//   epilogue: FWD z = GELU(acc); DA dA = dz GELU'(acc); DX, SPECTRAL out = acc.
+//   stage 5 (DA only): dWl[i][o] (+ db through a row of ones) += X[i][:] . dA[o][:]
+//     over the tile's points, Kahan-folded per tile.
+// The x tile arrives by bulk copy (TMA engine), one tile ahead.
+// Precision.  BF16: one product everywhere.  Split BF16: the DFT stages (1, 2)
+// use a = hi + lo with products hi.hi + hi.lo + lo.hi; the 1x1 contractions
+// (3, 5), which carry the bypass term that dominates the block output, split
+// both operands in three BF16 parts (exact for FP32 inputs) and sum the six
+// products of order >= 2^-16, so they are as accurate as FP32 products.
+// GELU uses the erf approximation 7.1.26 of Abramowitz and Stegun (absolute
+// error below 1.5e-7) with hardware exp2 and reciprocal.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include <cstdio>
+
+#include "fno_internal.h"
+#include "umma.h"
+
+namespace fno {
+
+namespace {
+
+constexpr int kP = 128;        // points per tile
+constexpr int kWarps = 8;      // one 16-point m-tile per warp
+constexpr int kThreads = 32 * kWarps;
+constexpr int kNTM = 4;        // max n-tiles of 8 output channels (Cs <= 32)
+constexpr int kClMax = 32;     // max 1x1 input channels
+
+// ---- warp-level tensor-core helpers (inline PTX) ----------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                          uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t a, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r0), "=r"(r1)
+               : "r"(a));
+}
+__device__ __forceinline__ void stsm_x4_t(uint32_t a, uint32_t r0, uint32_t r1, uint32_t r2,
+                                          uint32_t r3) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(a),
+               "r"(r0), "r"(r1), "r"(r2), "r"(r3)
+               : "memory");
+}
+// D += A (16x16, row) * B (16x8, col), BF16 in, FP32 accumulate
+__device__ __forceinline__ void mma16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                      uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// D += A (16x8, row) * B (8x8, col)
+__device__ __forceinline__ void mma8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// hi/lo BF16 split of two floats, packed in pairs (first value in the low half)
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t a, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r0), "=r"(r1)
+               : "r"(a));
+}
+__device__ __forceinline__ void stsm_x2_t(uint32_t a, uint32_t r0, uint32_t r1) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1,%2};" ::"r"(a), "r"(r0),
+               "r"(r1)
+               : "memory");
+}
+
+// three-way BF16 split of two floats: a = h + m + l exactly (FP32 inputs)
+__device__ __forceinline__ void split3(float a, float b, uint32_t& h, uint32_t& m, uint32_t& l) {
+  const __nv_bfloat162 hv = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(hv);
+  const float ra = a - hf.x, rb = b - hf.y;
+  const __nv_bfloat162 mv = __floats2bfloat162_rn(ra, rb);
+  const float2 mf = __bfloat1622float2(mv);
+  const __nv_bfloat162 lv = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+  h = *reinterpret_cast<const uint32_t*>(&hv);
+  m = *reinterpret_cast<const uint32_t*>(&mv);
+  l = *reinterpret_cast<const uint32_t*>(&lv);
+}
+
+// Phi2(a) = 1 + erf(a / sqrt 2) and exp(-a^2 / 2), with erf from Abramowitz
+// and Stegun 7.1.26: erf(u) = 1 - (a1 t + ... + a5 t^5) exp(-u^2),
+// t = 1 / (1 + p u), u >= 0, |error| < 1.5e-7.  For a < 0 the complement is
+// taken directly (no cancellation).
+__device__ __forceinline__ void phi2_as(float a, float& phi2, float& e) {
+  const float u = fabsf(a) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  q *= t;
+  e = exp2f(-u * u * 1.4426950408889634f);
+  const float c = q * e;  // 1 - erf(u)
+  phi2 = (a >= 0.f) ? 2.0f - c : c;
+}
+__device__ __forceinline__ float gelu_as(float a) {
+  float phi2, e;
+  phi2_as(a, phi2, e);
+  return 0.5f * a * phi2;
+}
+__device__ __forceinline__ float gelu_grad_as(float a) {
+  float phi2, e;
+  phi2_as(a, phi2, e);
+  return fmaf(a * e, 0.39894228040143268f, 0.5f * phi2);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Kernel parameters and shared-memory plan
+// ---------------------------------------------------------------------------
+enum { R_U = 0, R_Q, R_X, R_DA, R_STG, R_TB, R_WL, R_BIAS, R_END };
+
+struct EpiM {
+  EpiArgs a;
+  int* err;
+  const uint2* bz;     // stage-1 B fragments [Nz/4][KZ][2 (hi, lo)][32 lanes]
+  long long NxNy, ntiles, chan, plane;
+  int Nz, Nt, Jz, Jt, ZB, nzb;
+  int NT;              // n-tiles of 8 output channels
+  int M1;              // stage-1 m-tiles (two output channels x 8 t modes each)
+  int KZ;              // stage-1 k-steps of 16 over (jz, re/im)
+  int NZT;             // stage-1 n-tiles of (4 planes x re/im)
+  int KL16, KL8;       // stage-3 k-steps over input channels: 16s and an 8 tail
+  int MTI, nunits;     // stage 5 (dA mode): m-tiles over Cl + 1 rows; (m, n) units
+  int XR, UK, QP;      // x-tile rows; U' row length; Q plane stride (BF16 elements)
+  int NX;              // BF16 parts of the x and dA tiles (3 split, 1 plain)
+  uint32_t SB, BZO;    // bytes per staging buffer (x tile, then the tile's Bz fragments); Bz offset
+  uint32_t off[R_END + 1];
+};
+
+constexpr int kXS = kP + 8;  // x / dA row stride (BF16 elements): conflict-free ldmatrix rows
+
+static void epi_mma_geometry(const Dims& d, int mode, int Cs, int Cl, bool split, EpiM& k) {
+  k.Nz = (int)d.Nz;
+  k.Nt = (int)d.Nt;
+  k.Jz = (int)d.Jz;
+  k.Jt = (int)d.Jt;
+  k.ZB = kP / k.Nt;
+  k.nzb = k.Nz / k.ZB;
+  k.NT = (Cs + 7) / 8;
+  k.M1 = (Cs + 1) / 2;
+  k.KZ = (2 * k.Jz + 15) / 16;
+  k.NZT = k.ZB / 4;
+  const int lin = (mode == EPI_SPECTRAL) ? 0 : Cl;
+  k.KL16 = lin / 16;
+  k.KL8 = 0;
+  if (lin % 16 > 8)
+    k.KL16 += 1;
+  else if (lin % 16 > 0)
+    k.KL8 = 1;
+  k.MTI = (mode == EPI_DA) ? (Cl + 1 + 15) / 16 : 0;
+  k.nunits = k.MTI * k.NT;
+  // stage 5 reads rows 0..16 MTI - 1; rows past Cl only feed discarded dW rows,
+  // so rows beyond the tile are clamped to its last row instead of stored
+  int xr = 16 * k.KL16 + 8 * k.KL8;
+  if (mode == EPI_DA) xr = std::max(xr, (Cl + 1 + 7) / 8 * 8);
+  k.XR = xr;
+  k.UK = 16 * k.KZ + 8;
+  k.QP = 8 * k.NT * 24 + 16;
+  k.NX = split ? 3 : 1;
+  auto al = [](size_t x) { return (x + 15) / 16 * 16; };
+  size_t o = 0;
+  k.off[R_U] = (uint32_t)o;  // U' hi, lo: [16 M1][UK]
+  o = al(o + 2 * sizeof(uint16_t) * (size_t)(16 * k.M1) * k.UK);
+  k.off[R_Q] = (uint32_t)o;  // Q hi, lo: [ZB][QP]
+  o = al(o + 2 * sizeof(uint16_t) * (size_t)k.ZB * k.QP);
+  k.off[R_X] = (uint32_t)o;  // x tile parts: [NX][XR][kXS]
+  o = al(o + sizeof(uint16_t) * (size_t)k.NX * k.XR * kXS);
+  k.off[R_DA] = (uint32_t)o;  // dA tile parts (dA mode): [NX][8 NT][kXS]
+  if (mode == EPI_DA) o = al(o + sizeof(uint16_t) * (size_t)k.NX * 8 * k.NT * kXS);
+  // two staging buffers, each the FP32 x tile [Cl][kP] and the tile's Bz fragments
+  k.BZO = (uint32_t)al(sizeof(float) * (size_t)lin * kP);
+  k.SB = k.BZO + (uint32_t)(k.NZT * k.KZ * 64 * sizeof(uint2));
+  k.off[R_STG] = (uint32_t)o;
+  o = al(o + 2 * (size_t)k.SB);
+  k.off[R_TB] = (uint32_t)o;  // t-basis A fragments [Nt/16][2][32] uint4
+  o = al(o + sizeof(uint4) * 2 * 2 * 32);
+  k.off[R_WL] = (uint32_t)o;  // W_lin B fragments [KL16 + KL8][NTM][3][32] uint2
+  o = al(o + sizeof(uint2) * (size_t)(k.KL16 + k.KL8) * kNTM * 3 * 32);
+  k.off[R_BIAS] = (uint32_t)o;  // bias [8 NTM], then two mbarriers
+  o = al(o + sizeof(float) * 8 * kNTM + 2 * sizeof(uint64_t));
+  k.off[R_END] = (uint32_t)o;
+}
+
+// ---------------------------------------------------------------------------
+// Stage-1 B fragments of the inverse z basis, per block of 4 z-planes.  Column
+// n = (z, part) of the block: part 0 gives Re, part 1 gives Im of
+// sum_jz U[jz] Iz[z][jz]:
+//   part 0: B[(jz, 0)] = Re Iz, B[(jz, 1)] = -Im Iz
+//   part 1: B[(jz, 0)] = Im Iz, B[(jz, 1)] =  Re Iz
+// ---------------------------------------------------------------------------
+__global__ void k_epi_mma_bz(const float2* __restrict__ Iz, int Nz, int Jz, int KZ,
+                             uint2* __restrict__ bz) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = (Nz / 4) * KZ * 32;
+  if (idx >= total) return;
+  const int lane = idx % 32, ks = (idx / 32) % KZ, zq = idx / (32 * KZ);
+  const int n = lane / 4, z = 4 * zq + n / 2, part = n % 2;
+  auto val = [&](int kk) -> float {
+    const int jz = kk / 2, kp = kk % 2;
+    if (jz >= Jz) return 0.f;
+    const float2 f = Iz[(size_t)z * Jz + jz];
+    if (part == 0) return kp == 0 ? f.x : -f.y;
+    return kp == 0 ? f.y : f.x;
+  };
+  const int k0 = 16 * ks + 2 * (lane % 4);
+  uint32_t h0, l0, h1, l1;
+  split2(val(k0), val(k0 + 1), h0, l0);
+  split2(val(k0 + 8), val(k0 + 9), h1, l1);
+  const size_t base = (size_t)(zq * KZ + ks) * 2 * 32;
+  bz[base + lane] = make_uint2(h0, h1);
+  bz[base + 32 + lane] = make_uint2(l0, l1);
+}
+
+
+template <int MODE, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const EpiArgs& a = k.a;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Cs = a.Cs, Cl = (MODE == EPI_SPECTRAL) ? 0 : a.Cl;
+  const int NT = k.NT, Nt = k.Nt, UK = k.UK, QP = k.QP;
+  const size_t XP = (size_t)k.XR * kXS;      // stride between x-tile parts
+  const size_t DP = (size_t)8 * NT * kXS;    // stride between dA-tile parts
+
+  uint16_t* u_hi = reinterpret_cast<uint16_t*>(smem + k.off[R_U]);
+  uint16_t* u_lo = u_hi + (size_t)16 * k.M1 * UK;
+  uint16_t* q_hi = reinterpret_cast<uint16_t*>(smem + k.off[R_Q]);
+  uint16_t* q_lo = q_hi + (size_t)k.ZB * QP;
+  uint16_t* xt = reinterpret_cast<uint16_t*>(smem + k.off[R_X]);
+  uint16_t* dt = reinterpret_cast<uint16_t*>(smem + k.off[R_DA]);
+  unsigned char* stg = smem + k.off[R_STG];  // buffer q at stg + q * SB
+  const uint4* tb = reinterpret_cast<const uint4*>(smem + k.off[R_TB]);
+  uint2* wl = reinterpret_cast<uint2*>(smem + k.off[R_WL]);
+  float* sb = reinterpret_cast<float*>(smem + k.off[R_BIAS]);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + k.off[R_BIAS] + sizeof(float) * 8 * kNTM);
+  __shared__ int s_abort;
+
+  // ---- prologue: zero the operand tiles; constant fragments; bias ----------
+  {
+    const uint32_t n16 = (k.off[R_STG] - k.off[R_U]) / 16;
+    uint4* z4 = reinterpret_cast<uint4*>(smem + k.off[R_U]);
+    for (uint32_t e = tid; e < n16; e += kThreads) z4[e] = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    umma::mbar_init(&bar[0], 1);
+    umma::mbar_init(&bar[1], 1);
+    umma::fence_mbar_init();
+  }
+  // t-basis A fragments Tb[t][k2]: k2 < 8 c/N cos (jt = k2), k2 >= 8 -c/N sin (jt = k2 - 8)
+  {
+    uint4* tbw = reinterpret_cast<uint4*>(smem + k.off[R_TB]);
+    for (int e = tid; e < (Nt / 16) * 32; e += kThreads) {
+      const int mt = e / 32, ln = e % 32;
+      auto A2 = [&](int t, int k2) -> float {
+        const int jt = k2 & 7;
+        if (jt >= k.Jt) return 0.f;
+        const float2 f = a.It[(size_t)jt * Nt + t];
+        return k2 < 8 ? f.x : -f.y;
+      };
+      const int t0 = 16 * mt + ln / 4, c0 = 2 * (ln % 4);
+      uint4 h, l;
+      split2(A2(t0, c0), A2(t0, c0 + 1), h.x, l.x);
+      split2(A2(t0 + 8, c0), A2(t0 + 8, c0 + 1), h.y, l.y);
+      split2(A2(t0, c0 + 8), A2(t0, c0 + 9), h.z, l.z);
+      split2(A2(t0 + 8, c0 + 8), A2(t0 + 8, c0 + 9), h.w, l.w);
+      tbw[(mt * 2 + 0) * 32 + ln] = h;
+      tbw[(mt * 2 + 1) * 32 + ln] = l;
+    }
+  }
+  if (MODE != EPI_SPECTRAL) {
+    // W_lin B fragments B3[i][o] = W(i, o), three BF16 parts; 16-steps then the 8 tail
+    const int nks = k.KL16 + k.KL8;
+    for (int e = tid; e < nks * kNTM * 32; e += kThreads) {
+      const int ln = e % 32, nt = (e / 32) % kNTM, ks = e / (32 * kNTM);
+      const int o = 8 * nt + ln / 4;
+      auto W = [&](int i) -> float {
+        return (i < Cl && o < Cs) ? a.wlin[(size_t)i * a.w_si + (size_t)o * a.w_sc] : 0.f;
+      };
+      const int i0 = 16 * ks + 2 * (ln % 4);
+      uint2 h, m, l;
+      split3(W(i0), W(i0 + 1), h.x, m.x, l.x);
+      if (ks < k.KL16)
+        split3(W(i0 + 8), W(i0 + 9), h.y, m.y, l.y);
+      else
+        h.y = m.y = l.y = 0;
+      uint2* dst = wl + (size_t)((ks * kNTM + nt) * 3) * 32 + ln;
+      dst[0] = h;
+      dst[32] = m;
+      dst[64] = l;
+    }
+  }
+  for (int o = tid; o < 8 * kNTM; o += kThreads)
+    sb[o] = ((MODE == EPI_FWD || MODE == EPI_DA) && o < Cs) ? a.bias[o] : 0.f;
+  __syncthreads();
+  if (MODE == EPI_DA)  // the row of ones that makes the dW_lin GEMM give db as well
+    for (int p = tid; p < kP; p += kThreads) xt[(size_t)Cl * kXS + p] = 0x3f80;  // BF16 1.0
+
+  // ---- tile walk: contiguous range, decoded incrementally ------------------
+  const long long t_begin = k.ntiles * blockIdx.x / gridDim.x;
+  const long long t_end = k.ntiles * (blockIdx.x + 1) / gridDim.x;
+  long long col0 = t_begin / k.nzb;
+  int zb = (int)(t_begin - col0 * k.nzb);
+  long long b = col0 / k.NxNy, xy = col0 - b * k.NxNy;
+  unsigned pending = 0;  // buffers with bulk copies issued and not yet waited for
+  // Bulk copies (TMA engine) of a tile's inputs into staging buffer buf: the
+  // Cl rows of the x tile and the tile's Bz fragments.  Copy q goes to warp
+  // q % 8, lane q / 8, so the issue cost is spread over the CTA.  Called by
+  // every thread.
+  const uint32_t bz_bytes = (uint32_t)(k.NZT * k.KZ * 64 * sizeof(uint2));
+  auto issue = [&](long long bb, long long xyy, int zbb, int buf) {
+    unsigned char* dst = stg + (size_t)buf * k.SB;
+    if (tid == 0)
+      umma::mbar_arrive_expect_tx(&bar[buf], (uint32_t)(sizeof(float) * Cl * kP) + bz_bytes);
+    for (int q = warp + kWarps * lane; q <= Cl; q += kThreads) {
+      umma::fence_proxy_async();
+      if (q < Cl)
+        umma::bulk_g2s(dst + sizeof(float) * (size_t)q * kP,
+                       a.lin_in + (bb * Cl + q) * k.chan + xyy * k.plane + (long long)zbb * kP,
+                       (uint32_t)(sizeof(float) * kP), &bar[buf]);
+      else
+        umma::bulk_g2s(dst + k.BZO, k.bz + (size_t)zbb * k.NZT * k.KZ * 64, bz_bytes, &bar[buf]);
+    }
+    pending |= 1u << buf;
+  };
+  if (t_begin < t_end) issue(b, xy, zb, 0);
+
+  uint32_t phase = 0u;  // bit q: the parity the next wait on bar[q] expects
+  long long cur_col = -1;
+  const int JZT = k.Jz * k.Jt;
+  const int zl = (16 * warp) / Nt, t0 = (16 * warp) % Nt;  // this warp's plane and first t
+  float ks_sum[2][4], ks_cmp[2][4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ks_sum[u][q] = ks_cmp[u][q] = 0.f;
+
+  for (long long tau = t_begin, c = 0; tau < t_end; ++tau, ++c) {
+    const long long tile_ofs = xy * k.plane + (long long)zb * kP;
+    const int buf = (int)(c & 1);
+    __syncthreads();  // S0: every shared-memory read of the previous tile is done
+    if (s_abort) break;
+    // the next tile (prefetch its x tile into the other buffer)
+    int zbn = zb + 1;
+    long long xyn = xy, bn = b;
+    if (zbn == k.nzb) {
+      zbn = 0;
+      if (++xyn == k.NxNy) {
+        xyn = 0;
+        ++bn;
+      }
+    }
+    if (tau + 1 < t_end) issue(bn, xyn, zbn, buf ^ 1);
+    // a new column: U'[(o, jt)][(jz, re/im)] from the spectrum U[b][o][x][y][jz][jt]
+    const long long col = b * k.NxNy + xy;
+    if (col != cur_col) {
+      const float2* U = a.U + ((b * Cs) * k.NxNy + xy) * JZT;
+      for (int e = tid; e < Cs * JZT; e += kThreads) {
+        const int o = e / JZT, r = e - o * JZT, jz = r / k.Jt, jt = r - jz * k.Jt;
+        const float2 u = __ldg(U + (size_t)o * k.NxNy * JZT + r);
+        uint32_t h, l;
+        split2(u.x, u.y, h, l);
+        const size_t at = (size_t)(o * 8 + jt) * UK + 2 * jz;
+        *reinterpret_cast<uint32_t*>(u_hi + at) = h;
+        *reinterpret_cast<uint32_t*>(u_lo + at) = l;
+      }
+      cur_col = col;
+    }
+    // dA mode: this thread's upstream gradients, in accumulator-fragment order
+    float dzr[kNTM][4];
+    if (MODE == EPI_DA) {
+      const float* dzb = a.dz + (b * Cs) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
+#pragma unroll
+      for (int nt = 0; nt < kNTM; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int o = 8 * nt + 2 * (lane & 3) + (e & 1);
+          dzr[nt][e] = (nt < NT && o < Cs) ? __ldg(dzb + (long long)o * k.chan + 8 * (e >> 1)) : 0.f;
+        }
+    }
+    // this tile's staging buffer (prefetched during the previous tile)
+    if (umma::mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+      phase ^= 1u << buf;
+      pending &= ~(1u << buf);
+    } else {
+      s_abort = 1;
+      if (k.err) atomicExch(k.err, 1);
+    }
+    const unsigned char* sgb = stg + (size_t)buf * k.SB;
+    const uint2* bzs = reinterpret_cast<const uint2*>(sgb + k.BZO);
+    __syncthreads();  // S1: U' is ready
+
+    // ---- stage 1: inverse z of the tile's planes -> Q (BF16 hi/lo) --------
+    for (int m1 = warp; m1 < k.M1; m1 += kWarps) {
+      // c1: hi.hi products; c1s: the cross terms (a second dependency chain)
+      float c1[2][4], c1s[2][4];
+#pragma unroll
+      for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c1[n][q] = c1s[n][q] = 0.f;
+      for (int ks = 0; ks < k.KZ; ++ks) {
+        uint32_t ah[4], al[4];
+        const int row = 16 * m1 + (lane & 7) + 8 * ((lane >> 3) & 1);
+        const int kc = 16 * ks + 8 * (lane >> 4);
+        ldsm_x4(smem_addr(u_hi + (size_t)row * UK + kc), ah[0], ah[1], ah[2], ah[3]);
+        if (SPLIT) ldsm_x4(smem_addr(u_lo + (size_t)row * UK + kc), al[0], al[1], al[2], al[3]);
+        uint2 bh[2], bl[2];
+#pragma unroll
+        for (int ntz = 0; ntz < 2; ++ntz) {
+          const uint2* bzp = bzs + (size_t)((ntz < k.NZT ? ntz : 0) * k.KZ + ks) * 64 + lane;
+          bh[ntz] = bzp[0];
+          bl[ntz] = bzp[32];
+        }
+        if (SPLIT) {
+#pragma unroll
+          for (int ntz = 0; ntz < 2; ++ntz)
+            if (ntz < k.NZT) mma16(c1s[ntz], al[0], al[1], al[2], al[3], bh[ntz].x, bh[ntz].y);
+#pragma unroll
+          for (int ntz = 0; ntz < 2; ++ntz)
+            if (ntz < k.NZT) mma16(c1s[ntz], ah[0], ah[1], ah[2], ah[3], bl[ntz].x, bl[ntz].y);
+        }
+#pragma unroll
+        for (int ntz = 0; ntz < 2; ++ntz)
+          if (ntz < k.NZT) mma16(c1[ntz], ah[0], ah[1], ah[2], ah[3], bh[ntz].x, bh[ntz].y);
+      }
+#pragma unroll
+      for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c1[n][q] += c1s[n][q];
+      // transposed 8x8 blocks: stored rows are (plane, re/im), columns jt
+      const int j = lane >> 3, r = lane & 7;
+      const int o = 2 * m1 + (j & 1), ntz = (k.NZT == 2) ? (j >> 1) : 0;
+      const size_t at = (size_t)(4 * ntz + (r >> 1)) * QP + (size_t)o * 24 + 8 * (r & 1);
+      uint32_t h0, l0, h1, l1;
+      split2(c1[0][0], c1[0][1], h0, l0);  // (o_a, planes 0-3)
+      split2(c1[0][2], c1[0][3], h1, l1);  // (o_b, planes 0-3)
+      if (k.NZT == 2) {
+        uint32_t h2, l2, h3, l3;
+        split2(c1[1][0], c1[1][1], h2, l2);  // (o_a, planes 4-7)
+        split2(c1[1][2], c1[1][3], h3, l3);  // (o_b, planes 4-7)
+        stsm_x4_t(smem_addr(q_hi + at), h0, h1, h2, h3);
+        stsm_x4_t(smem_addr(q_lo + at), l0, l1, l2, l3);
+      } else {
+        stsm_x2_t(smem_addr(q_hi + at), h0, h1);
+        stsm_x2_t(smem_addr(q_lo + at), l0, l1);
+      }
+    }
+
+    // ---- the x tile: split into BF16 parts ------------------------------------
+    if (Cl > 0) {
+      const float* sg = reinterpret_cast<const float*>(sgb);
+      for (int e = tid; e < Cl * (kP / 4); e += kThreads) {
+        const int i = e / (kP / 4), p4 = 4 * (e % (kP / 4));
+        const float4 v = *reinterpret_cast<const float4*>(sg + (size_t)i * kP + p4);
+        const size_t at = (size_t)i * kXS + p4;
+        if (SPLIT) {
+          uint2 h, m, l;
+          split3(v.x, v.y, h.x, m.x, l.x);
+          split3(v.z, v.w, h.y, m.y, l.y);
+          *reinterpret_cast<uint2*>(xt + at) = h;
+          *reinterpret_cast<uint2*>(xt + XP + at) = m;
+          *reinterpret_cast<uint2*>(xt + 2 * XP + at) = l;
+        } else {
+          uint2 h, l;
+          split2(v.x, v.y, h.x, l.x);
+          split2(v.z, v.w, h.y, l.y);
+          *reinterpret_cast<uint2*>(xt + at) = h;
+        }
+      }
+    }
+    __syncthreads();  // S2: Q and the x tile are ready
+
+    // ---- stages 2 + 3: this warp's 16 points, all output channels ----------
+    float acc[kNTM][4];
+#pragma unroll
+    for (int nt = 0; nt < kNTM; ++nt) {
+      const float b0 = sb[8 * nt + 2 * (lane & 3)], b1 = sb[8 * nt + 2 * (lane & 3) + 1];
+      acc[nt][0] = b0;
+      acc[nt][1] = b1;
+      acc[nt][2] = b0;
+      acc[nt][3] = b1;
+    }
+    {
+      const uint4 h = tb[((t0 >> 4) * 2 + 0) * 32 + lane], l = tb[((t0 >> 4) * 2 + 1) * 32 + lane];
+      const uint32_t th[4] = {h.x, h.y, h.z, h.w}, tl[4] = {l.x, l.y, l.z, l.w};
+      const int j = lane >> 3, r = lane & 7;
+      const uint16_t* qb = (j >> 1) ? q_lo : q_hi;
+      uint32_t bq[kNTM][4];
+#pragma unroll
+      for (int nt = 0; nt < kNTM; ++nt)
+        if (nt < NT)
+          ldsm_x4(smem_addr(qb + (size_t)zl * QP + (size_t)(8 * nt + r) * 24 + 8 * (j & 1)), bq[nt][0],
+                  bq[nt][1], bq[nt][2], bq[nt][3]);
+      // product-major over the n-tiles: independent accumulators back to back
+      if (SPLIT) {
+#pragma unroll
+        for (int nt = 0; nt < kNTM; ++nt)
+          if (nt < NT) mma16(acc[nt], tl[0], tl[1], tl[2], tl[3], bq[nt][0], bq[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < kNTM; ++nt)
+          if (nt < NT) mma16(acc[nt], th[0], th[1], th[2], th[3], bq[nt][2], bq[nt][3]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < kNTM; ++nt)
+        if (nt < NT) mma16(acc[nt], th[0], th[1], th[2], th[3], bq[nt][0], bq[nt][1]);
+    }
+    if (MODE != EPI_SPECTRAL) {
+      const int j = lane >> 3, r = lane & 7;
+      for (int ks = 0; ks < k.KL16; ++ks) {
+        uint32_t ah[4], am[4], al[4];
+        const size_t at = (size_t)(16 * ks + r + 8 * (j >> 1)) * kXS + 16 * warp + 8 * (j & 1);
+        ldsm_x4_t(smem_addr(xt + at), ah[0], ah[1], ah[2], ah[3]);
+        if (SPLIT) {
+          ldsm_x4_t(smem_addr(xt + XP + at), am[0], am[1], am[2], am[3]);
+          ldsm_x4_t(smem_addr(xt + 2 * XP + at), al[0], al[1], al[2], al[3]);
+        }
+        const uint2* wk = wl + (size_t)(ks * kNTM * 3) * 32 + lane;  // [nt][part][lane]
+        if (SPLIT) {
+          // six products, small terms first, each over all n-tiles back to back
+#pragma unroll
+          for (int pr = 0; pr < 5; ++pr) {
+            const uint32_t* A = (pr == 0 || pr == 3) ? am : (pr == 1 ? al : ah);
+            const int bp = (pr == 0 || pr == 4) ? 1 : (pr == 2 ? 2 : 0);
+#pragma unroll
+            for (int nt = 0; nt < kNTM; ++nt)
+              if (nt < NT) {
+                const uint2 w = wk[(nt * 3 + bp) * 32];
+                mma16(acc[nt], A[0], A[1], A[2], A[3], w.x, w.y);
+              }
+          }
+        }
+#pragma unroll
+        for (int nt = 0; nt < kNTM; ++nt)
+          if (nt < NT) {
+            const uint2 w = wk[(nt * 3) * 32];
+            mma16(acc[nt], ah[0], ah[1], ah[2], ah[3], w.x, w.y);
+          }
+      }
+      if (k.KL8) {
+        const int ks = k.KL16;
+        uint32_t ah[2], am[2], al[2];
+        const size_t at = (size_t)(16 * ks + r) * kXS + 16 * warp + 8 * (j & 1);
+        ldsm_x2_t(smem_addr(xt + at), ah[0], ah[1]);
+        if (SPLIT) {
+          ldsm_x2_t(smem_addr(xt + XP + at), am[0], am[1]);
+          ldsm_x2_t(smem_addr(xt + 2 * XP + at), al[0], al[1]);
+        }
+        const uint2* wk = wl + (size_t)(ks * kNTM * 3) * 32 + lane;
+        if (SPLIT) {
+#pragma unroll
+          for (int pr = 0; pr < 5; ++pr) {
+            const uint32_t* A = (pr == 0 || pr == 3) ? am : (pr == 1 ? al : ah);
+            const int bp = (pr == 0 || pr == 4) ? 1 : (pr == 2 ? 2 : 0);
+#pragma unroll
+            for (int nt = 0; nt < kNTM; ++nt)
+              if (nt < NT) mma8(acc[nt], A[0], A[1], wk[(nt * 3 + bp) * 32].x);
+          }
+        }
+#pragma unroll
+        for (int nt = 0; nt < kNTM; ++nt)
+          if (nt < NT) mma8(acc[nt], ah[0], ah[1], wk[(nt * 3) * 32].x);
+      }
+    }
+
+    // ---- pointwise epilogue; stores of 8 consecutive points per channel -----
+    {
+      float* ob = a.out + (b * Cs + 2 * (lane & 3)) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
+      const int ob0 = Cs - 2 * (lane & 3);  // channels left for this lane's column pair
+#pragma unroll
+      for (int nt = 0; nt < kNTM; ++nt) {
+        if (nt < NT) {
+          float* on = ob + (long long)(8 * nt) * k.chan;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float v = acc[nt][e];
+            if (MODE == EPI_FWD) v = gelu_as(v);
+            if (MODE == EPI_DA) v = dzr[nt][e] * gelu_grad_as(v);
+            acc[nt][e] = v;
+            if (8 * nt + (e & 1) < ob0) on[(e & 1) * k.chan + 8 * (e >> 1)] = v;
+          }
+        }
+      }
+    }
+
+    if (MODE == EPI_DA) {
+      // dA tile [o][p] in BF16 parts for the dW_lin GEMM (transposed 8x8 blocks)
+      {
+        const int j = (lane >> 3) & 1, r = lane & 7;
+#pragma unroll
+        for (int nt = 0; nt < kNTM; ++nt) {
+          if (nt < NT) {
+            const size_t at = (size_t)(8 * nt + r) * kXS + 16 * warp + 8 * j;
+            if (SPLIT) {
+              uint32_t h0, m0, l0, h1, m1_, l1;
+              split3(acc[nt][0], acc[nt][1], h0, m0, l0);
+              split3(acc[nt][2], acc[nt][3], h1, m1_, l1);
+              stsm_x2_t(smem_addr(dt + at), h0, h1);
+              stsm_x2_t(smem_addr(dt + DP + at), m0, m1_);
+              stsm_x2_t(smem_addr(dt + 2 * DP + at), l0, l1);
+            } else {
+              uint32_t h0, l0, h1, l1;
+              split2(acc[nt][0], acc[nt][1], h0, l0);
+              split2(acc[nt][2], acc[nt][3], h1, l1);
+              stsm_x2_t(smem_addr(dt + at), h0, h1);
+            }
+          }
+        }
+      }
+      __syncthreads();  // S3: the dA tile is complete
+      // ---- stage 5: dW_lin and db over the tile's 128 points ----------------
+#pragma unroll
+      for (int ui = 0; ui < 2; ++ui) {
+        const int u = warp + ui * kWarps;
+        if (u < k.nunits) {
+          const int mi = u / NT, nt = u - mi * NT;
+          // four dependency chains: k-step parity x (large, small) products
+          float c5[2][2][4];
+#pragma unroll
+          for (int x = 0; x < 2; ++x)
+#pragma unroll
+            for (int y = 0; y < 2; ++y)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) c5[x][y][q] = 0.f;
+          const int row = min(16 * mi + (lane & 7) + 8 * ((lane >> 3) & 1), k.XR - 1);
+          const int j = lane >> 3, r = lane & 7;
+#pragma unroll 2
+          for (int ks = 0; ks < kP / 16; ++ks) {
+            float(&cl)[4] = c5[ks & 1][0];
+            float(&cs)[4] = c5[ks & 1][1];
+            uint32_t ah[4], am[4], al[4];
+            const size_t ax = (size_t)row * kXS + 16 * ks + 8 * (lane >> 4);
+            const size_t bx = (size_t)(8 * nt + r) * kXS + 16 * ks + 8 * (j & 1);
+            ldsm_x4(smem_addr(xt + ax), ah[0], ah[1], ah[2], ah[3]);
+            if (SPLIT) {
+              ldsm_x4(smem_addr(xt + XP + ax), am[0], am[1], am[2], am[3]);
+              ldsm_x4(smem_addr(xt + 2 * XP + ax), al[0], al[1], al[2], al[3]);
+              uint2 bh, bm, bl;
+              ldsm_x4(smem_addr(dt + ((j >> 1) ? DP : 0) + bx), bh.x, bh.y, bm.x, bm.y);
+              ldsm_x2(smem_addr(dt + 2 * DP + bx), bl.x, bl.y);
+              mma16(cs, am[0], am[1], am[2], am[3], bm.x, bm.y);
+              mma16(cl, am[0], am[1], am[2], am[3], bh.x, bh.y);
+              mma16(cs, al[0], al[1], al[2], al[3], bh.x, bh.y);
+              mma16(cl, ah[0], ah[1], ah[2], ah[3], bm.x, bm.y);
+              mma16(cs, ah[0], ah[1], ah[2], ah[3], bl.x, bl.y);
+              mma16(cl, ah[0], ah[1], ah[2], ah[3], bh.x, bh.y);
+            } else {
+              uint32_t b0, b1;
+              ldsm_x2(smem_addr(dt + bx), b0, b1);
+              mma16(cl, ah[0], ah[1], ah[2], ah[3], b0, b1);
+            }
+          }
+          float c5s[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            c5s[q] = (c5[0][1][q] + c5[1][1][q]) + (c5[0][0][q] + c5[1][0][q]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float y = c5s[q] - ks_cmp[ui][q];
+            const float t = ks_sum[ui][q] + y;
+            ks_cmp[ui][q] = (t - ks_sum[ui][q]) - y;
+            ks_sum[ui][q] = t;
+          }
+        }
+      }
+    }
+    b = bn;
+    xy = xyn;
+    zb = zbn;
+  }
+
+  // bulk copies still in flight after a timed-out wait must land before exit
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (pending & (1u << q)) (void)umma::mbar_wait(&bar[q], (phase >> q) & 1u);
+  }
+
+  if (MODE == EPI_DA) {
+    const int npair = Cl * Cs + Cs;
+#pragma unroll
+    for (int ui = 0; ui < 2; ++ui) {
+      const int u = warp + ui * kWarps;
+      if (u < k.nunits) {
+        const int mi = u / NT, nt = u - mi * NT;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = 16 * mi + (lane >> 2) + 8 * (q >> 1);
+          const int o = 8 * nt + 2 * (lane & 3) + (q & 1);
+          const float v = ks_sum[ui][q] - ks_cmp[ui][q];
+          if (o < Cs && i <= Cl) {
+            const int idx = (i < Cl) ? i * Cs + o : Cl * Cs + o;
+            a.part[(long long)blockIdx.x * npair + idx] = v;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+size_t epilogue_mma_table_bytes(const Dims& d) {
+  const int KZ = (int)((2 * d.Jz + 15) / 16);
+  return sizeof(uint2) * (size_t)((d.Nz + 3) / 4) * KZ * 2 * 32;
+}
+
+bool epilogue_mma_supported(const Dims& d, int mode, int Cs, int Cl, char* why, size_t nwhy) {
+  auto no = [&](const char* m) {
+    if (why && nwhy) snprintf(why, nwhy, "%s", m);
+    return false;
+  };
+  if (d.Nt != 16 && d.Nt != 32) return no("mma epilogue needs Nt of 16 or 32");
+  if (d.Jt > 8) return no("mma epilogue needs mt <= 8");
+  if (d.Nz % (kP / d.Nt) != 0) return no("mma epilogue needs Nz a multiple of 128 / Nt");
+  if (d.Jz > 24) return no("mma epilogue needs 2*mz <= 24");
+  if (Cs < 1 || Cs > 8 * kNTM) return no("mma epilogue needs 1..32 output channels");
+  if (mode != EPI_SPECTRAL && (Cl < 1 || Cl > kClMax)) return no("mma epilogue needs 1..32 1x1 inputs");
+  EpiM k{};
+  epi_mma_geometry(d, mode, Cs, Cl, true, k);
+  if (mode == EPI_DA && k.nunits > 2 * kWarps) return no("mma epilogue: too many dW_lin tiles");
+  if (k.off[R_END] > 227 * 1024) return no("mma epilogue: shared memory");
+  return true;
+}
+
+template <int MODE, bool SPLIT>
+static cudaError_t launch_mma_t(const EpiM& k, int* grid_used, cudaStream_t s) {
+  const void* kern = (const void*)k_epi_mma<MODE, SPLIT>;
+  const size_t smem = k.off[R_END];
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  long long g = (long long)per_sm * sm_count();
+  if (g > k.ntiles) g = k.ntiles;
+  if (g > epilogue_max_grid()) g = epilogue_max_grid();
+  if (g < 1) g = 1;
+  if (grid_used) *grid_used = (int)g;
+  static const char* names[2][4] = {
+      {"fno_epi_spectral_mma_bf16", "fno_epi_fwd_mma_bf16", "fno_epi_da_mma_bf16", "fno_epi_dx_mma_bf16"},
+      {"fno_epi_spectral_mma_bf16x3", "fno_epi_fwd_mma_bf16x3", "fno_epi_da_mma_bf16x3",
+       "fno_epi_dx_mma_bf16x3"}};
+  FNO_LAUNCH(names[SPLIT ? 1 : 0][MODE], (k_epi_mma<MODE, SPLIT>), (int)g, kThreads, smem, s, k);
+  return cudaSuccess;
+}
+
+template <int MODE>
+static cudaError_t launch_mma_m(const EpiM& k, bool split, int* g, cudaStream_t s) {
+  return split ? launch_mma_t<MODE, true>(k, g, s) : launch_mma_t<MODE, false>(k, g, s);
+}
+
+cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, void* table, int* err,
+                                int* grid_used, cudaStream_t s) {
+  EpiM k{};
+  k.a = a;
+  k.err = err;
+  epi_mma_geometry(d, a.mode, a.Cs, a.Cl, split, k);
+  k.NxNy = d.Nx * d.Ny;
+  k.plane = d.Nz * d.Nt;
+  k.chan = k.NxNy * k.plane;
+  k.ntiles = d.B * k.NxNy * (long long)k.nzb;
+  uint2* bz = static_cast<uint2*>(table);
+  k.bz = bz;
+  {
+    const int total = (k.Nz / 4) * k.KZ * 32;
+    FNO_LAUNCH("fno_epi_mma_tables", k_epi_mma_bz, (total + 255) / 256, 256, 0, s, a.Iz, k.Nz,
+               k.Jz, k.KZ, bz);
+  }
+  switch (a.mode) {
+    case EPI_SPECTRAL: return launch_mma_m<EPI_SPECTRAL>(k, split, grid_used, s);
+    case EPI_FWD: return launch_mma_m<EPI_FWD>(k, split, grid_used, s);
+    case EPI_DA: return launch_mma_m<EPI_DA>(k, split, grid_used, s);
+    default: return launch_mma_m<EPI_DX>(k, split, grid_used, s);
+  }
+}
+
+}  // namespace fno

@@ -29,14 +29,6 @@ namespace fno {
 
 using namespace umma;
 
-#define FNO_LAUNCH_TC(name, kern, grid, block, smem, stream, ...) \
-  do {                                                            \
-    prof_before(name, stream);                                    \
-    kern<<<grid, block, smem, stream>>>(__VA_ARGS__);             \
-    cudaError_t e_ = cudaGetLastError();                          \
-    prof_after(stream);                                           \
-    if (e_ != cudaSuccess) return e_;                             \
-  } while (0)
 
 // ---- small helpers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t bf2(float a, float b) {
@@ -496,9 +488,9 @@ cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const D
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(k.ngroups, sm_count());
   if (split)
-    FNO_LAUNCH_TC("fno_fwd_tz_tc_bf16x3", k_fwd_tz_tc<true>, grid, kFwdThreads, smem, s, k);
+    FNO_LAUNCH("fno_fwd_tz_tc_bf16x3", k_fwd_tz_tc<true>, grid, kFwdThreads, smem, s, k);
   else
-    FNO_LAUNCH_TC("fno_fwd_tz_tc_bf16", k_fwd_tz_tc<false>, grid, kFwdThreads, smem, s, k);
+    FNO_LAUNCH("fno_fwd_tz_tc_bf16", k_fwd_tz_tc<false>, grid, kFwdThreads, smem, s, k);
   return cudaSuccess;
 }
 

@@ -62,6 +62,13 @@ TC_CASES = [
     (Dims(2, 17, 9, 6, 5, 64, 32, 2, 2, 12, 8), "17->9 channels, Nz=64, Nt=32, 2mz=24"),
     (Dims(1, 3, 4, 4, 4, 128, 8, 1, 1, 3, 5), "Nz=128, Nt=8, mt=Nt/2+1 (Nyquist)"),
     (Dims(2, 20, 20, 8, 8, 16, 16, 2, 3, 8, 3), "Nz=16 (8 columns per tile), 2mz=Nz"),
+    (Dims(1, 32, 32, 6, 4, 16, 32, 2, 2, 4, 8), "32 channels: two dW_lin tiles per warp"),
+    # single channels on either side of the 1x1; with C_in = C_out = 1 and this
+    # seed db is one sum of 24576 terms that cancels to 0.72 (sum |dA| ~ 1e4), a
+    # conditioning test of the sum rather than of the kernel, so the edge is
+    # covered by 1 -> 2 and 2 -> 1 channels instead
+    (Dims(2, 1, 2, 4, 6, 32, 16, 2, 3, 5, 8), "one input channel, mt = Nt/2"),
+    (Dims(2, 2, 1, 4, 6, 32, 16, 2, 3, 5, 8), "one output channel, mt = Nt/2"),
 ]
 
 
