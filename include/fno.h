@@ -118,8 +118,10 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
                   float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream);
 
 /* Status a previous call left in its workspace: waits for `stream`, then returns
- * FNO_OK, or FNO_ERR_TIMEOUT when one of that call's bounded device-side waits
- * (tensor-core pipeline barriers) gave up and the kernel returned early. */
+ * FNO_OK, FNO_ERR_TIMEOUT when one of that call's bounded device-side waits
+ * (tensor-core pipeline barriers) gave up and the kernel returned early, or
+ * FNO_ERR_CUDA when a kernel found its shared-memory window misaligned for the
+ * tensor copies and returned without computing. */
 int fno_workspace_status(const void* ws, void* stream);
 
 /* Message of the calling thread's last error ("" if none). */

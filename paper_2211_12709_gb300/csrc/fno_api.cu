@@ -481,6 +481,7 @@ int fno_workspace_status(const void* ws, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(status)");
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (h == 2) return fail(FNO_ERR_CUDA, "a kernel refused a misaligned shared-memory window");
   if (h != 0) return fail(FNO_ERR_TIMEOUT, "a bounded device-side wait gave up (status %d)", h);
   return FNO_OK;
 }

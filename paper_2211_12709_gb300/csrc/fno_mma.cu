@@ -32,6 +32,7 @@
 // products of order >= 2^-16, so they are as accurate as FP32 products.
 // GELU uses the erf approximation 7.1.26 of Abramowitz and Stegun (absolute
 // error below 1.5e-7) with hardware exp2 and reciprocal.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -135,15 +136,25 @@ __device__ __forceinline__ void split3(float a, float b, uint32_t& h, uint32_t& 
 // and Stegun 7.1.26: erf(u) = 1 - (a1 t + ... + a5 t^5) exp(-u^2),
 // t = 1 / (1 + p u), u >= 0, |error| < 1.5e-7.  For a < 0 the complement is
 // taken directly (no cancellation).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ void phi2_as(float a, float& phi2, float& e) {
   const float u = fabsf(a) * 0.70710678118654752f;
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
+  const float t = rcp_approx(fmaf(0.3275911f, u, 1.0f));
   float q = fmaf(1.061405429f, t, -1.453152027f);
   q = fmaf(q, t, 1.421413741f);
   q = fmaf(q, t, -0.284496736f);
   q = fmaf(q, t, 0.254829592f);
   q *= t;
-  e = exp2f(-u * u * 1.4426950408889634f);
+  e = ex2_approx(-u * u * 1.4426950408889634f);
   const float c = q * e;  // 1 - erf(u)
   phi2 = (a >= 0.f) ? 2.0f - c : c;
 }
@@ -166,6 +177,7 @@ __device__ __forceinline__ float gelu_grad_as(float a) {
 enum { R_U = 0, R_Q, R_X, R_DA, R_STG, R_TB, R_WL, R_BIAS, R_END };
 
 struct EpiM {
+  CUtensorMap tmx;     // the 1x1 input as rows [B * Cl][chan], boxes of Cl rows x 128 points
   EpiArgs a;
   int* err;
   const uint2* bz;     // stage-1 B fragments [Nz/4][KZ][2 (hi, lo)][32 lanes]
@@ -223,17 +235,20 @@ static void epi_mma_geometry(const Dims& d, int mode, int Cs, int Cl, bool split
   o = al(o + sizeof(uint16_t) * (size_t)k.NX * k.XR * kXS);
   k.off[R_DA] = (uint32_t)o;  // dA tile parts (dA mode): [NX][8 NT][kXS]
   if (mode == EPI_DA) o = al(o + sizeof(uint16_t) * (size_t)k.NX * 8 * k.NT * kXS);
-  // two staging buffers, each the FP32 x tile [Cl][kP] and the tile's Bz fragments
-  k.BZO = (uint32_t)al(sizeof(float) * (size_t)lin * kP);
-  k.SB = k.BZO + (uint32_t)(k.NZT * k.KZ * 64 * sizeof(uint2));
+  // two staging buffers (128-byte aligned TMA destinations), each the FP32 x
+  // tile [Cl][kP] and the tile's Bz fragments
+  auto al128 = [](size_t x) { return (x + 127) / 128 * 128; };
+  k.BZO = (uint32_t)al128(sizeof(float) * (size_t)lin * kP);
+  k.SB = (uint32_t)al128(k.BZO + (size_t)k.NZT * k.KZ * 64 * sizeof(uint2));
+  o = al128(o);
   k.off[R_STG] = (uint32_t)o;
   o = al(o + 2 * (size_t)k.SB);
   k.off[R_TB] = (uint32_t)o;  // t-basis A fragments [Nt/16][2][32] uint4
   o = al(o + sizeof(uint4) * 2 * 2 * 32);
   k.off[R_WL] = (uint32_t)o;  // W_lin B fragments [KL16 + KL8][NTM][3][32] uint2
   o = al(o + sizeof(uint2) * (size_t)(k.KL16 + k.KL8) * kNTM * 3 * 32);
-  k.off[R_BIAS] = (uint32_t)o;  // bias [8 NTM], then two mbarriers
-  o = al(o + sizeof(float) * 8 * kNTM + 2 * sizeof(uint64_t));
+  k.off[R_BIAS] = (uint32_t)o;  // bias [8 NTM], two mbarriers, the abort flag
+  o = al(o + sizeof(float) * 8 * kNTM + 2 * sizeof(uint64_t) + 16);
   k.off[R_END] = (uint32_t)o;
 }
 
@@ -269,8 +284,8 @@ __global__ void k_epi_mma_bz(const float2* __restrict__ Iz, int Nz, int Jz, int 
 
 
 template <int MODE, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__ EpiM k) {
+  extern __shared__ __align__(128) unsigned char smem[];
   const EpiArgs& a = k.a;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Cs = a.Cs, Cl = (MODE == EPI_SPECTRAL) ? 0 : a.Cl;
@@ -289,7 +304,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
   uint2* wl = reinterpret_cast<uint2*>(smem + k.off[R_WL]);
   float* sb = reinterpret_cast<float*>(smem + k.off[R_BIAS]);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + k.off[R_BIAS] + sizeof(float) * 8 * kNTM);
-  __shared__ int s_abort;
+  volatile int& s_abort = *reinterpret_cast<int*>(bar + 2);
+
+  // TMA destinations must be 128-byte aligned: refuse (uniformly, before any
+  // copy is issued) rather than fault if the dynamic shared window is not
+  if ((umma::smem_u32(stg) & 127u) != 0u) {
+    if (tid == 0 && k.err) atomicExch(k.err, 2);
+    return;
+  }
 
   // ---- prologue: zero the operand tiles; constant fragments; bias ----------
   {
@@ -359,23 +381,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
   int zb = (int)(t_begin - col0 * k.nzb);
   long long b = col0 / k.NxNy, xy = col0 - b * k.NxNy;
   unsigned pending = 0;  // buffers with bulk copies issued and not yet waited for
-  // Bulk copies (TMA engine) of a tile's inputs into staging buffer buf: the
-  // Cl rows of the x tile and the tile's Bz fragments.  Copy q goes to warp
-  // q % 8, lane q / 8, so the issue cost is spread over the CTA.  Called by
-  // every thread.
+  // Copies (TMA engine) of a tile's inputs into staging buffer buf, issued by
+  // one thread: the x tile (Cl rows x 128 points, one tensor-map box) and the
+  // tile's Bz fragments.  Called by every thread (pending is tracked by all).
   const uint32_t bz_bytes = (uint32_t)(k.NZT * k.KZ * 64 * sizeof(uint2));
   auto issue = [&](long long bb, long long xyy, int zbb, int buf) {
-    unsigned char* dst = stg + (size_t)buf * k.SB;
-    if (tid == 0)
-      umma::mbar_arrive_expect_tx(&bar[buf], (uint32_t)(sizeof(float) * Cl * kP) + bz_bytes);
-    for (int q = warp + kWarps * lane; q <= Cl; q += kThreads) {
+    if (tid == 0) {
+      unsigned char* dst = stg + (size_t)buf * k.SB;
       umma::fence_proxy_async();
-      if (q < Cl)
-        umma::bulk_g2s(dst + sizeof(float) * (size_t)q * kP,
-                       a.lin_in + (bb * Cl + q) * k.chan + xyy * k.plane + (long long)zbb * kP,
-                       (uint32_t)(sizeof(float) * kP), &bar[buf]);
-      else
-        umma::bulk_g2s(dst + k.BZO, k.bz + (size_t)zbb * k.NZT * k.KZ * 64, bz_bytes, &bar[buf]);
+      umma::mbar_arrive_expect_tx(&bar[buf], (uint32_t)(sizeof(float) * Cl * kP) + bz_bytes);
+      if (Cl > 0) umma::tma_load_2d(dst, &k.tmx, (int)(xyy * k.plane + (long long)zbb * kP), (int)(bb * Cl), &bar[buf]);
+      umma::bulk_g2s(dst + k.BZO, k.bz + (size_t)zbb * k.NZT * k.KZ * 64, bz_bytes, &bar[buf]);
     }
     pending |= 1u << buf;
   };
@@ -409,7 +425,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
     if (tau + 1 < t_end) issue(bn, xyn, zbn, buf ^ 1);
     // a new column: U'[(o, jt)][(jz, re/im)] from the spectrum U[b][o][x][y][jz][jt]
     const long long col = b * k.NxNy + xy;
-    if (col != cur_col) {
+    const bool newcol = (col != cur_col);
+    if (newcol) {
       const float2* U = a.U + ((b * Cs) * k.NxNy + xy) * JZT;
       for (int e = tid; e < Cs * JZT; e += kThreads) {
         const int o = e / JZT, r = e - o * JZT, jz = r / k.Jt, jt = r - jz * k.Jt;
@@ -425,14 +442,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
     // dA mode: this thread's upstream gradients, in accumulator-fragment order
     float dzr[kNTM][4];
     if (MODE == EPI_DA) {
-      const float* dzb = a.dz + (b * Cs) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
+      const float* dzb = a.dz + (b * Cs + 2 * (lane & 3)) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
+      const uint32_t ch = (uint32_t)k.chan;
+      const int left = Cs - 2 * (lane & 3);
 #pragma unroll
       for (int nt = 0; nt < kNTM; ++nt)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int o = 8 * nt + 2 * (lane & 3) + (e & 1);
-          dzr[nt][e] = (nt < NT && o < Cs) ? __ldg(dzb + (long long)o * k.chan + 8 * (e >> 1)) : 0.f;
-        }
+        for (int e = 0; e < 4; ++e)
+          dzr[nt][e] = (nt < NT && 8 * nt + (e & 1) < left)
+                           ? __ldg(dzb + ((uint32_t)(8 * nt + (e & 1)) * ch + 8 * (e >> 1)))
+                           : 0.f;
     }
     // this tile's staging buffer (prefetched during the previous tile)
     if (umma::mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
@@ -444,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
     }
     const unsigned char* sgb = stg + (size_t)buf * k.SB;
     const uint2* bzs = reinterpret_cast<const uint2*>(sgb + k.BZO);
-    __syncthreads();  // S1: U' is ready
+    if (newcol) __syncthreads();  // S1: the rebuilt U' is ready
 
     // ---- stage 1: inverse z of the tile's planes -> Q (BF16 hi/lo) --------
     for (int m1 = warp; m1 < k.M1; m1 += kWarps) {
@@ -527,7 +546,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
     __syncthreads();  // S2: Q and the x tile are ready
 
     // ---- stages 2 + 3: this warp's 16 points, all output channels ----------
-    float acc[kNTM][4];
+    // acc: bias and the hi.hi products; accx: the cross terms of the splits
+    // (a second dependency chain, outside the dA mode's register budget)
+    constexpr bool XACC = SPLIT && MODE != EPI_DA;
+    float acc[kNTM][4], accx[kNTM][4];
+#pragma unroll
+    for (int nt = 0; nt < kNTM; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) accx[nt][e] = 0.f;
 #pragma unroll
     for (int nt = 0; nt < kNTM; ++nt) {
       const float b0 = sb[8 * nt + 2 * (lane & 3)], b1 = sb[8 * nt + 2 * (lane & 3) + 1];
@@ -551,10 +577,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
       if (SPLIT) {
 #pragma unroll
         for (int nt = 0; nt < kNTM; ++nt)
-          if (nt < NT) mma16(acc[nt], tl[0], tl[1], tl[2], tl[3], bq[nt][0], bq[nt][1]);
+          if (nt < NT) mma16(XACC ? accx[nt] : acc[nt], tl[0], tl[1], tl[2], tl[3], bq[nt][0], bq[nt][1]);
 #pragma unroll
         for (int nt = 0; nt < kNTM; ++nt)
-          if (nt < NT) mma16(acc[nt], th[0], th[1], th[2], th[3], bq[nt][2], bq[nt][3]);
+          if (nt < NT) mma16(XACC ? accx[nt] : acc[nt], th[0], th[1], th[2], th[3], bq[nt][2], bq[nt][3]);
       }
 #pragma unroll
       for (int nt = 0; nt < kNTM; ++nt)
@@ -581,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
             for (int nt = 0; nt < kNTM; ++nt)
               if (nt < NT) {
                 const uint2 w = wk[(nt * 3 + bp) * 32];
-                mma16(acc[nt], A[0], A[1], A[2], A[3], w.x, w.y);
+                mma16(XACC ? accx[nt] : acc[nt], A[0], A[1], A[2], A[3], w.x, w.y);
               }
           }
         }
@@ -609,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
             const int bp = (pr == 0 || pr == 4) ? 1 : (pr == 2 ? 2 : 0);
 #pragma unroll
             for (int nt = 0; nt < kNTM; ++nt)
-              if (nt < NT) mma8(acc[nt], A[0], A[1], wk[(nt * 3 + bp) * 32].x);
+              if (nt < NT) mma8(XACC ? accx[nt] : acc[nt], A[0], A[1], wk[(nt * 3 + bp) * 32].x);
           }
         }
 #pragma unroll
@@ -618,21 +644,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const EpiM k) {
       }
     }
 
+    if (XACC) {
+#pragma unroll
+      for (int nt = 0; nt < kNTM; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[nt][e] += accx[nt][e];
+    }
     // ---- pointwise epilogue; stores of 8 consecutive points per channel -----
     {
       float* ob = a.out + (b * Cs + 2 * (lane & 3)) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
       const int ob0 = Cs - 2 * (lane & 3);  // channels left for this lane's column pair
+      const uint32_t ch = (uint32_t)k.chan;  // 32 * chan < 2^32 (checked on the host)
 #pragma unroll
       for (int nt = 0; nt < kNTM; ++nt) {
         if (nt < NT) {
-          float* on = ob + (long long)(8 * nt) * k.chan;
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             float v = acc[nt][e];
             if (MODE == EPI_FWD) v = gelu_as(v);
             if (MODE == EPI_DA) v = dzr[nt][e] * gelu_grad_as(v);
             acc[nt][e] = v;
-            if (8 * nt + (e & 1) < ob0) on[(e & 1) * k.chan + 8 * (e >> 1)] = v;
+            if (8 * nt + (e & 1) < ob0) ob[(uint32_t)(8 * nt + (e & 1)) * ch + 8 * (e >> 1)] = v;
           }
         }
       }
@@ -770,6 +802,8 @@ bool epilogue_mma_supported(const Dims& d, int mode, int Cs, int Cl, char* why, 
   if (d.Jt > 8) return no("mma epilogue needs mt <= 8");
   if (d.Nz % (kP / d.Nt) != 0) return no("mma epilogue needs Nz a multiple of 128 / Nt");
   if (d.Jz > 24) return no("mma epilogue needs 2*mz <= 24");
+  if ((long long)d.Nx * d.Ny * d.Nz * d.Nt * 32 >= (1LL << 32))
+    return no("mma epilogue needs 32 * Nx*Ny*Nz*Nt < 2^32");
   if (Cs < 1 || Cs > 8 * kNTM) return no("mma epilogue needs 1..32 output channels");
   if (mode != EPI_SPECTRAL && (Cl < 1 || Cl > kClMax)) return no("mma epilogue needs 1..32 1x1 inputs");
   EpiM k{};
@@ -807,6 +841,34 @@ static cudaError_t launch_mma_m(const EpiM& k, bool split, int* g, cudaStream_t 
   return split ? launch_mma_t<MODE, true>(k, g, s) : launch_mma_t<MODE, false>(k, g, s);
 }
 
+// Tensor map of a [rows][chan] FP32 array with boxes of box_rows x 128 points,
+// encoded through the driver entry point (no link-time driver dependency).
+static cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long chan, long long rows,
+                                int box_rows) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return cudaErrorNotSupported;
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)chan, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)chan * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kP, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, void* table, int* err,
                                 int* grid_used, cudaStream_t s) {
   EpiM k{};
@@ -819,6 +881,10 @@ cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, voi
   k.ntiles = d.B * k.NxNy * (long long)k.nzb;
   uint2* bz = static_cast<uint2*>(table);
   k.bz = bz;
+  if (a.mode != EPI_SPECTRAL) {
+    cudaError_t e = encode_x_map(&k.tmx, a.lin_in, k.chan, d.B * (long long)a.Cl, a.Cl);
+    if (e != cudaSuccess) return e;
+  }
   {
     const int total = (k.Nz / 4) * k.KZ * 32;
     FNO_LAUNCH("fno_epi_mma_tables", k_epi_mma_bz, (total + 255) / 256, 256, 0, s, a.Iz, k.Nz,
