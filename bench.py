@@ -168,11 +168,12 @@ def roofline_of(name, per_launch_ms, dd, pk, precision):
     gbs = nbytes / sec / 1e9
     tfl = nflops / sec / 1e12
     f_hbm = gbs / pk["hbm_gbs"]
-    if "_tc" in name:
-        # split BF16 issues three products per real multiply-add
-        tf_issued = tfl * (3 if name.endswith("bf16x3") else 1)
-        comp = {"bound": "tensor", "achieved": round(tf_issued, 2), "peak": pk["bf16_tflops"],
-                "unit": "TFLOP/s", "frac": round(tf_issued / pk["bf16_tflops"], 4),
+    if "_tc_" in name or "_mma_" in name:
+        # tensor-core kernels (tcgen05 or mma.sync): algorithmic flops against
+        # the dense BF16 peak; split BF16 issues 3 (DFT stages) or 6 (1x1
+        # stages) products per real multiply-add, which the fraction leaves out
+        comp = {"bound": "tensor", "achieved": round(tfl, 2), "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": round(tfl / pk["bf16_tflops"], 4),
                 "peak_src": pk["src"] + " cuBLAS bf16 burst"}
     else:
         ap = alu_peak_tflops(pk)
