@@ -228,6 +228,26 @@ def precision_sweep(args, step_of, outs, stream, barrier, units):
     return runs
 
 
+def replica_seed(rank: int) -> int:
+    """Input-configuration index of a replica: independent replicas draw different seeds."""
+    return 4 + rank
+
+
+def reduce_step_time(ms: float, dist=None, device=None) -> float:
+    """Max of the per-rank step times (the slowest replica sets the job's pace)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: int, world: int, ms: float) -> float:
+    """Gpoint*ch/s of the whole job: every rank's units over the slowest step time."""
+    return units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def oracle_sample_time(wl_name, sample_channels, seed=1000):
     """Seconds of one oracle fwd+bwd on the workload grid with fewer channels, and its units."""
     import numpy as np
@@ -316,7 +336,7 @@ def main():
     B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[args.workload]
     modes = (mx, my, mz, mt)
     Ng = Nx * Ny * Nz * Nt
-    cfg = 4 + rank  # independent replicas draw different seeds
+    cfg = replica_seed(rank)
     # inputs in pinned host memory (the e2e leg copies them every step)
     x_h = torch.from_numpy(inputs.grf((B, C), (Nx, Ny, Nz, Nt), ell, inputs.SEED_INPUT + cfg)).pin_memory()
     dz_h = torch.from_numpy(inputs.normal((B, C, Nx, Ny, Nz, Nt), inputs.SEED_UPSTREAM + cfg)).pin_memory()
@@ -377,13 +397,9 @@ def main():
     prof = _lib.fno_profile_stop()
     launches = _lib.fno_launch_count() - n0
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_step_time(e0.elapsed_time(e1) / args.steps, dist, dev)
     units = B * C * Ng
-    value = units * world / (ms * 1e-3) / 1e9
+    value = whole_job_value(units, world, ms)
 
     # ---- end to end: pinned host inputs -> C ABI -> host results ----
     e2e = None
@@ -404,12 +420,8 @@ def main():
                 hbuf.copy_(dbuf, non_blocking=True)
         e3.record(stream)
         barrier()
-        ms2 = e2.elapsed_time(e3) / k2
-        if dist is not None:
-            t = torch.tensor([ms2], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms2 = float(t.item())
-        e2e = {"value": units * world / (ms2 * 1e-3) / 1e9, "unit": UNIT,
+        ms2 = reduce_step_time(e2.elapsed_time(e3) / k2, dist, dev)
+        e2e = {"value": whole_job_value(units, world, ms2), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms2}
 
     # ---- roofline of the dominant kernel ----

@@ -162,3 +162,21 @@ def test_repeated_calls_are_bitwise_deterministic():
     c = run_block(d, x, w, wl, b, dz, "fp32")
     for u, v in zip(a, c):
         assert np.array_equal(u, v)
+
+
+def test_workspace_status_word_reports_timeout_and_misalignment_codes():
+    # The status word at the start of the workspace is what a kernel sets when a
+    # bounded wait gives up (1) or its shared window is misaligned (2); planting
+    # the codes by hand checks the host-side reporting without any kernel failing.
+    from paper_2211_12709_gb300 import _lib
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    status = ws.view(torch.int32)
+    _lib.fno_workspace_status(ws.data_ptr(), 0)                 # 0: OK
+    status[0] = 1
+    with pytest.raises(_lib.FnoError) as ei:
+        _lib.fno_workspace_status(ws.data_ptr(), 0)
+    assert ei.value.status == -5                                # FNO_ERR_TIMEOUT
+    status[0] = 2
+    with pytest.raises(_lib.FnoError) as ei:
+        _lib.fno_workspace_status(ws.data_ptr(), 0)
+    assert ei.value.status == -4                                # FNO_ERR_CUDA
