@@ -151,6 +151,9 @@ TRAFFIC_PER_UNIT = {
     "fno_epi_fwd_f32": (0.805e9 + 0.6312e9) / 167772160,
     "fno_epi_da_f32": (1.476e9 + 0.646e9) / 167772160,
     "fno_epi_dx_f32": (0.8049e9 + 0.6129e9) / 167772160,
+    "fno_epi_fwd_mma_bf16x3": (0.800946e9 + 0.6336622e9) / 167772160,
+    "fno_epi_da_mma_bf16x3": (1.470072e9 + 0.646274e9) / 167772160,
+    "fno_fwd_tz_tc_bf16x3": (0.6712366e9 + 0.1125819e9) / 167772160,
 }
 
 
