@@ -233,6 +233,14 @@ static int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
 
 static bool is_tc(int precision) { return precision == FNO_BF16 || precision == FNO_BF16X3; }
 
+// One complex axis: mma.sync for the tensor-core precisions, FP32 otherwise.
+static cudaError_t line(const float2* in, float2* out, int64_t outer, int nin, int nout, int64_t inner,
+                        const float2* tab, int precision, cudaStream_t s) {
+  if (is_tc(precision) && line_mma_supported(nin, nout))
+    return launch_line_mma(in, out, outer, nin, nout, inner, tab, precision == FNO_BF16X3, s);
+  return launch_line_f32(in, out, outer, nin, nout, inner, tab, s);
+}
+
 // Forward kept-mode spectrum of C channels of src into out: t,z per column
 // (tensor cores for the BF16 precisions) -> y -> x.  Uses t1, t2.
 static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2* ft,
@@ -242,16 +250,16 @@ static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2
     CK(launch_fwd_tz_tc(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, precision == FNO_BF16X3, err, s));
   else
     CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
-  CK(launch_line_f32(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, s));
-  CK(launch_line_f32(t2, out, d.B * C, (int)d.Nx, (int)d.Jx, d.Jy * d.Jz * d.Jt, T.Fx, s));
+  CK(line(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, precision, s));
+  CK(line(t2, out, d.B * C, (int)d.Nx, (int)d.Jx, d.Jy * d.Jz * d.Jt, T.Fx, precision, s));
   return FNO_OK;
 }
 
 // Inverse x then y of C channels of kept spectra into u1 = [B][C][Nx][Ny][Jz][Jt].
 static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tables& T, float2* t2,
-                          float2* u1, cudaStream_t s) {
-  CK(launch_line_f32(sp, t2, d.B * C, (int)d.Jx, (int)d.Nx, d.Jy * d.Jz * d.Jt, T.Ix, s));
-  CK(launch_line_f32(t2, u1, d.B * C * d.Nx, (int)d.Jy, (int)d.Ny, d.Jz * d.Jt, T.Iy, s));
+                          float2* u1, cudaStream_t s, int precision = FNO_FP32) {
+  CK(line(sp, t2, d.B * C, (int)d.Jx, (int)d.Nx, d.Jy * d.Jz * d.Jt, T.Ix, precision, s));
+  CK(line(t2, u1, d.B * C * d.Nx, (int)d.Jy, (int)d.Ny, d.Jz * d.Jt, T.Iy, precision, s));
   return FNO_OK;
 }
 
@@ -290,7 +298,7 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   CK(launch_tables(d, T, err, s));
   if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
   CK(launch_mix_f32(d, xh, reinterpret_cast<const float2*>(w), yh, s));
-  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s))) return rc;
+  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
   EpiArgs a{};
   a.mode = (op == FNO_OP_BLOCK_FWD) ? EPI_FWD : EPI_SPECTRAL;
   a.U = t1;
@@ -376,7 +384,7 @@ int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const 
   CK(launch_mix_adjoint_f32(d, xh, reinterpret_cast<const float2*>(w), g,
                             reinterpret_cast<float2*>(dw), dx ? gxh : nullptr, s));
   if (dx) {
-    if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s))) return rc;
+    if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s, precision))) return rc;
     EpiArgs a{};
     a.mode = EPI_SPECTRAL;
     a.U = t1;
@@ -432,7 +440,7 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   // recompute the forward spectrum and the spectral partial U1 of the output
   if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
   CK(launch_mix_f32(d, xh, wc, yh, s));
-  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s))) return rc;
+  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
   // dA = dz GELU'(A) with the partial sums of dW_lin and db
   EpiArgs a{};
   a.mode = EPI_DA;
@@ -456,7 +464,7 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s, precision, err))) return rc;
   CK(launch_mix_adjoint_f32(d, xh, wc, yh, reinterpret_cast<float2*>(dw), gxh, s));
   // dX = inverse(GXh) + W_lin dA
-  if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s))) return rc;
+  if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s, precision))) return rc;
   EpiArgs q{};
   q.mode = EPI_DX;
   q.U = t1;

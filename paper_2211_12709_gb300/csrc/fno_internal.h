@@ -92,6 +92,12 @@ size_t epilogue_mma_table_bytes(const Dims& d);
 cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, void* table, int* err,
                                 int* grid_used, cudaStream_t s);
 
+// One complex DFT axis on mma.sync (fno_mma.cu), BF16 (one product) or split
+// BF16 (three-way splits, six products); same contract as launch_line_f32.
+bool line_mma_supported(int nin, int nout);
+cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int nin, int nout,
+                            int64_t inner, const float2* tab, bool split, cudaStream_t s);
+
 // ---- tensor-core path (fno_tc.cu) -------------------------------------------
 // Pruned DFT over t then z on tcgen05 (BF16 or split BF16); same contract as
 // launch_fwd_tz_f32.  err: device word set to nonzero when a bounded wait gives up.

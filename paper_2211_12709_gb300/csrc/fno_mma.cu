@@ -899,3 +899,218 @@ cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, voi
 }
 
 }  // namespace fno
+
+namespace fno {
+
+// ---------------------------------------------------------------------------
+// One complex DFT axis on the tensor cores (the y and x stages of Alg. 2, both
+// directions):  out[o][q][i] = sum_n T[q][n] in[o][n][i]   (complex).
+// As a real GEMM per o: rows m = 2q + (re, im) of the output, k = 2n + (re, im)
+// of the input, columns i:
+//   A[(q,0)][(n,0)] = Re T, A[(q,0)][(n,1)] = -Im T, A[(q,1)][(n,0)] = Im T,
+//   A[(q,1)][(n,1)] = Re T;  B[(n, part)][i] = part of in[o][n][i].
+// A B-fragment slot pair (2 t4, 2 t4 + 1) is exactly one input float2.  Each
+// warp computes 16 columns of one o; with few m-tiles (M <= 64) it streams K,
+// otherwise it holds all of K for its columns and walks the m-tiles.  Split
+// BF16 uses three-way splits of both operands (six products), BF16 one product.
+// ---------------------------------------------------------------------------
+struct LineM {
+  const float2* in;
+  float2* out;
+  const float2* tab;  // [nout][nin]
+  long long outer, inner, ncb;  // ncb: 16-column blocks per o
+  int nin, nout, MT, KS;
+};
+
+constexpr int kLineMTMax = 4;  // m-tiles held at once when streaming K
+constexpr int kLineKSMax = 4;  // k-steps held at once when walking m-tiles
+
+template <bool SPLIT, bool KOUTER>
+__global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint4* af = reinterpret_cast<uint4*>(smem);  // [MT][KS][parts][32 lanes]
+  constexpr int NP = SPLIT ? 3 : 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int MT = L.MT, KS = L.KS, nin = L.nin, nout = L.nout;
+
+  // ---- A fragments of the basis, once per CTA ----------------------------
+  for (int e = tid; e < MT * KS * 32; e += 256) {
+    const int ln = e % 32, ks = (e / 32) % KS, mt = e / (32 * KS);
+    auto A = [&](int m, int kk) -> float {
+      const int q = m >> 1, po = m & 1, n = kk >> 1, pi = kk & 1;
+      if (q >= nout || n >= nin) return 0.f;
+      const float2 t = L.tab[(size_t)q * nin + n];
+      if (po == 0) return pi == 0 ? t.x : -t.y;
+      return pi == 0 ? t.y : t.x;
+    };
+    const int r0 = 16 * mt + ln / 4, c0 = 16 * ks + 2 * (ln % 4);
+    uint4 h, m, l;
+    split3(A(r0, c0), A(r0, c0 + 1), h.x, m.x, l.x);
+    split3(A(r0 + 8, c0), A(r0 + 8, c0 + 1), h.y, m.y, l.y);
+    split3(A(r0, c0 + 8), A(r0, c0 + 9), h.z, m.z, l.z);
+    split3(A(r0 + 8, c0 + 8), A(r0 + 8, c0 + 9), h.w, m.w, l.w);
+    uint4* dst = af + ((size_t)(mt * KS + ks) * NP) * 32 + ln;
+    dst[0] = h;
+    if (SPLIT) {
+      dst[32] = m;
+      dst[64] = l;
+    }
+  }
+  __syncthreads();
+
+  const long long ntask = L.outer * L.ncb;
+  const long long nw = (long long)gridDim.x * 8;
+  for (long long task = (long long)blockIdx.x * 8 + warp; task < ntask; task += nw) {
+    const long long o = task / L.ncb;
+    const long long i0 = (task - o * L.ncb) * 16;
+    const float2* src = L.in + (size_t)o * nin * L.inner;
+    float2* dst = L.out + (size_t)o * nout * L.inner;
+    // B fragments of k-step ks for the two n-tiles of this warp's 16 columns
+    auto loadB = [&](int ks, uint32_t (&bh)[2][2], uint32_t (&bm)[2][2], uint32_t (&bl)[2][2]) {
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const long long col = i0 + 8 * nt + g8;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int n = 8 * ks + 4 * hf + t4;
+          float2 v = make_float2(0.f, 0.f);
+          if (n < nin && col < L.inner) v = __ldg(src + (size_t)n * L.inner + col);
+          if (SPLIT)
+            split3(v.x, v.y, bh[nt][hf], bm[nt][hf], bl[nt][hf]);
+          else {
+            uint32_t lo;
+            split2(v.x, v.y, bh[nt][hf], lo);
+          }
+        }
+      }
+    };
+    // C fragment of m-tile mt, n-tile nt -> out (re on even rows, im on odd rows)
+    auto store = [&](int mt, int nt, const float (&c)[4]) {
+      const float p0 = __shfl_xor_sync(0xffffffffu, c[0], 4), p1 = __shfl_xor_sync(0xffffffffu, c[1], 4);
+      const float p2 = __shfl_xor_sync(0xffffffffu, c[2], 4), p3 = __shfl_xor_sync(0xffffffffu, c[3], 4);
+      const bool even = (g8 & 1) == 0;
+      // even rows g: (q, re) and (q + 4, re); the partner lane holds the im parts
+      const int q = (16 * mt + (g8 & ~1)) / 2 + (even ? 0 : 4);
+      const float4 v = even ? make_float4(c[0], p0, c[1], p1) : make_float4(p2, c[2], p3, c[3]);
+      const long long col = i0 + 8 * nt + 2 * t4;
+      if (q < nout && col + 1 < L.inner && (L.inner & 1) == 0)
+        *reinterpret_cast<float4*>(dst + (size_t)q * L.inner + col) = v;
+      else if (q < nout) {
+        if (col < L.inner) dst[(size_t)q * L.inner + col] = make_float2(v.x, v.y);
+        if (col + 1 < L.inner) dst[(size_t)q * L.inner + col + 1] = make_float2(v.z, v.w);
+      }
+    };
+    auto mma_parts = [&](float (&d)[4], const uint4* a, const uint32_t (&bh)[2], const uint32_t (&bm)[2],
+                         const uint32_t (&bl)[2]) {
+      const uint4 ah = a[0];
+      if (SPLIT) {
+        const uint4 am = a[32], al = a[64];
+        mma16(d, am.x, am.y, am.z, am.w, bm[0], bm[1]);
+        mma16(d, al.x, al.y, al.z, al.w, bh[0], bh[1]);
+        mma16(d, ah.x, ah.y, ah.z, ah.w, bl[0], bl[1]);
+        mma16(d, am.x, am.y, am.z, am.w, bh[0], bh[1]);
+        mma16(d, ah.x, ah.y, ah.z, ah.w, bm[0], bm[1]);
+      }
+      mma16(d, ah.x, ah.y, ah.z, ah.w, bh[0], bh[1]);
+    };
+    if (KOUTER) {
+      // few m-tiles: stream K, all m-tiles and both n-tiles in registers
+      float acc[kLineMTMax][2][4];
+#pragma unroll
+      for (int mt = 0; mt < kLineMTMax; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+      for (int ks = 0; ks < KS; ++ks) {
+        uint32_t bh[2][2], bm[2][2], bl[2][2];
+        loadB(ks, bh, bm, bl);
+#pragma unroll
+        for (int mt = 0; mt < kLineMTMax; ++mt)
+          if (mt < MT) {
+            const uint4* a = af + ((size_t)(mt * KS + ks) * NP) * 32 + lane;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_parts(acc[mt][nt], a, bh[nt], bm[nt], bl[nt]);
+          }
+      }
+#pragma unroll
+      for (int mt = 0; mt < kLineMTMax; ++mt)
+        if (mt < MT)
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) store(mt, nt, acc[mt][nt]);
+    } else {
+      // few k-steps: every B fragment of the columns in registers, walk the m-tiles
+      uint32_t bh[kLineKSMax][2][2], bm[kLineKSMax][2][2], bl[kLineKSMax][2][2];
+#pragma unroll
+      for (int ks = 0; ks < kLineKSMax; ++ks)
+        if (ks < KS) loadB(ks, bh[ks], bm[ks], bl[ks]);
+      for (int mt = 0; mt < MT; ++mt) {
+        float acc[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kLineKSMax; ++ks)
+          if (ks < KS) {
+            const uint4* a = af + ((size_t)(mt * KS + ks) * NP) * 32 + lane;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_parts(acc[nt], a, bh[ks][nt], bm[ks][nt], bl[ks][nt]);
+          }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) store(mt, nt, acc[nt]);
+      }
+    }
+  }
+}
+
+bool line_mma_supported(int nin, int nout) {
+  const int MT = (2 * nout + 15) / 16, KS = (2 * nin + 15) / 16;
+  return MT <= kLineMTMax || KS <= kLineKSMax;
+}
+
+cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int nin, int nout,
+                            int64_t inner, const float2* tab, bool split, cudaStream_t s) {
+  if (outer <= 0 || inner <= 0) return cudaSuccess;
+  LineM L{};
+  L.in = in;
+  L.out = out;
+  L.tab = tab;
+  L.outer = outer;
+  L.inner = inner;
+  L.ncb = (inner + 15) / 16;
+  L.nin = nin;
+  L.nout = nout;
+  L.MT = (2 * nout + 15) / 16;
+  L.KS = (2 * nin + 15) / 16;
+  const bool kouter = L.MT <= kLineMTMax;
+  if (!kouter && L.KS > kLineKSMax) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(uint4) * (size_t)L.MT * L.KS * (split ? 3 : 1) * 32;
+  const void* kern = split ? (kouter ? (const void*)k_line_mma<true, true> : (const void*)k_line_mma<true, false>)
+                           : (kouter ? (const void*)k_line_mma<false, true> : (const void*)k_line_mma<false, false>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long tasks = outer * L.ncb;
+  long long g = (long long)per_sm * sm_count();
+  if (g * 8 > tasks) g = (tasks + 7) / 8;
+  if (g < 1) g = 1;
+  const char* name = split ? "fno_line_mma_bf16x3" : "fno_line_mma_bf16";
+  if (split) {
+    if (kouter)
+      FNO_LAUNCH(name, (k_line_mma<true, true>), (int)g, 256, smem, s, L);
+    else
+      FNO_LAUNCH(name, (k_line_mma<true, false>), (int)g, 256, smem, s, L);
+  } else {
+    if (kouter)
+      FNO_LAUNCH(name, (k_line_mma<false, true>), (int)g, 256, smem, s, L);
+    else
+      FNO_LAUNCH(name, (k_line_mma<false, false>), (int)g, 256, smem, s, L);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fno
