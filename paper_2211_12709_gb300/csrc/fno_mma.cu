@@ -53,6 +53,7 @@ constexpr int kWarps = 8;      // one 16-point m-tile per warp
 constexpr int kThreads = 32 * kWarps;
 constexpr int kNTM = 4;        // max n-tiles of 8 output channels (Cs <= 32)
 constexpr int kClMax = 32;     // max 1x1 input channels
+constexpr int kKZMax = 3;      // stage-1 k-steps (2 * mz <= 24)
 
 // ---- warp-level tensor-core helpers (inline PTX) ----------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -466,58 +467,84 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
     if (newcol) __syncthreads();  // S1: the rebuilt U' is ready
 
     // ---- stage 1: inverse z of the tile's planes -> Q (BF16 hi/lo) --------
-    for (int m1 = warp; m1 < k.M1; m1 += kWarps) {
-      // c1: hi.hi products; c1s: the cross terms (a second dependency chain)
-      float c1[2][4], c1s[2][4];
+    // warp w owns m-tiles w and w + 8 (when M1 > 8); both run interleaved
+    {
+      const bool two = warp + kWarps < k.M1;
+      if (warp < k.M1) {
+        // c1: hi.hi products; c1s: the cross terms (a second dependency chain)
+        float c1[2][2][4], c1s[2][2][4];
 #pragma unroll
-      for (int n = 0; n < 2; ++n)
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) c1[n][q] = c1s[n][q] = 0.f;
-      for (int ks = 0; ks < k.KZ; ++ks) {
-        uint32_t ah[4], al[4];
-        const int row = 16 * m1 + (lane & 7) + 8 * ((lane >> 3) & 1);
-        const int kc = 16 * ks + 8 * (lane >> 4);
-        ldsm_x4(smem_addr(u_hi + (size_t)row * UK + kc), ah[0], ah[1], ah[2], ah[3]);
-        if (SPLIT) ldsm_x4(smem_addr(u_lo + (size_t)row * UK + kc), al[0], al[1], al[2], al[3]);
-        uint2 bh[2], bl[2];
+          for (int n = 0; n < 2; ++n)
 #pragma unroll
-        for (int ntz = 0; ntz < 2; ++ntz) {
-          const uint2* bzp = bzs + (size_t)((ntz < k.NZT ? ntz : 0) * k.KZ + ks) * 64 + lane;
-          bh[ntz] = bzp[0];
-          bl[ntz] = bzp[32];
+            for (int q = 0; q < 4; ++q) c1[u][n][q] = c1s[u][n][q] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kKZMax; ++ks) {
+          if (ks < k.KZ) {
+            uint32_t ah[2][4], al[2][4];
+            const int kc = 16 * ks + 8 * (lane >> 4);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (u == 0 || two) {
+                const int row = 16 * (warp + u * kWarps) + (lane & 7) + 8 * ((lane >> 3) & 1);
+                ldsm_x4(smem_addr(u_hi + (size_t)row * UK + kc), ah[u][0], ah[u][1], ah[u][2], ah[u][3]);
+                if (SPLIT)
+                  ldsm_x4(smem_addr(u_lo + (size_t)row * UK + kc), al[u][0], al[u][1], al[u][2], al[u][3]);
+              }
+            }
+            uint2 bh[2], bl[2];
+#pragma unroll
+            for (int ntz = 0; ntz < 2; ++ntz) {
+              const uint2* bzp = bzs + (size_t)((ntz < k.NZT ? ntz : 0) * k.KZ + ks) * 64 + lane;
+              bh[ntz] = bzp[0];
+              bl[ntz] = bzp[32];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (u == 0 || two) {
+#pragma unroll
+                for (int ntz = 0; ntz < 2; ++ntz) {
+                  if (ntz < k.NZT) {
+                    if (SPLIT) {
+                      mma16(c1s[u][ntz], al[u][0], al[u][1], al[u][2], al[u][3], bh[ntz].x, bh[ntz].y);
+                      mma16(c1s[u][ntz], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[ntz].x, bl[ntz].y);
+                    }
+                    mma16(c1[u][ntz], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bh[ntz].x, bh[ntz].y);
+                  }
+                }
+              }
+            }
+          }
         }
-        if (SPLIT) {
 #pragma unroll
-          for (int ntz = 0; ntz < 2; ++ntz)
-            if (ntz < k.NZT) mma16(c1s[ntz], al[0], al[1], al[2], al[3], bh[ntz].x, bh[ntz].y);
+        for (int u = 0; u < 2; ++u) {
+          if (u == 0 || two) {
+            const int m1 = warp + u * kWarps;
+            float(&cc)[2][4] = c1[u];
 #pragma unroll
-          for (int ntz = 0; ntz < 2; ++ntz)
-            if (ntz < k.NZT) mma16(c1s[ntz], ah[0], ah[1], ah[2], ah[3], bl[ntz].x, bl[ntz].y);
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) cc[n][q] += c1s[u][n][q];
+            // transposed 8x8 blocks: stored rows are (plane, re/im), columns jt
+            const int j = lane >> 3, r = lane & 7;
+            const int o = 2 * m1 + (j & 1), ntz = (k.NZT == 2) ? (j >> 1) : 0;
+            const size_t at = (size_t)(4 * ntz + (r >> 1)) * QP + (size_t)o * 24 + 8 * (r & 1);
+            uint32_t h0, l0, h1, l1;
+            split2(cc[0][0], cc[0][1], h0, l0);  // (o_a, planes 0-3)
+            split2(cc[0][2], cc[0][3], h1, l1);  // (o_b, planes 0-3)
+            if (k.NZT == 2) {
+              uint32_t h2, l2, h3, l3;
+              split2(cc[1][0], cc[1][1], h2, l2);  // (o_a, planes 4-7)
+              split2(cc[1][2], cc[1][3], h3, l3);  // (o_b, planes 4-7)
+              stsm_x4_t(smem_addr(q_hi + at), h0, h1, h2, h3);
+              stsm_x4_t(smem_addr(q_lo + at), l0, l1, l2, l3);
+            } else {
+              stsm_x2_t(smem_addr(q_hi + at), h0, h1);
+              stsm_x2_t(smem_addr(q_lo + at), l0, l1);
+            }
+          }
         }
-#pragma unroll
-        for (int ntz = 0; ntz < 2; ++ntz)
-          if (ntz < k.NZT) mma16(c1[ntz], ah[0], ah[1], ah[2], ah[3], bh[ntz].x, bh[ntz].y);
-      }
-#pragma unroll
-      for (int n = 0; n < 2; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) c1[n][q] += c1s[n][q];
-      // transposed 8x8 blocks: stored rows are (plane, re/im), columns jt
-      const int j = lane >> 3, r = lane & 7;
-      const int o = 2 * m1 + (j & 1), ntz = (k.NZT == 2) ? (j >> 1) : 0;
-      const size_t at = (size_t)(4 * ntz + (r >> 1)) * QP + (size_t)o * 24 + 8 * (r & 1);
-      uint32_t h0, l0, h1, l1;
-      split2(c1[0][0], c1[0][1], h0, l0);  // (o_a, planes 0-3)
-      split2(c1[0][2], c1[0][3], h1, l1);  // (o_b, planes 0-3)
-      if (k.NZT == 2) {
-        uint32_t h2, l2, h3, l3;
-        split2(c1[1][0], c1[1][1], h2, l2);  // (o_a, planes 4-7)
-        split2(c1[1][2], c1[1][3], h3, l3);  // (o_b, planes 4-7)
-        stsm_x4_t(smem_addr(q_hi + at), h0, h1, h2, h3);
-        stsm_x4_t(smem_addr(q_lo + at), l0, l1, l2, l3);
-      } else {
-        stsm_x2_t(smem_addr(q_hi + at), h0, h1);
-        stsm_x2_t(smem_addr(q_lo + at), l0, l1);
       }
     }
 
@@ -588,7 +615,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
     }
     if (MODE != EPI_SPECTRAL) {
       const int j = lane >> 3, r = lane & 7;
-      for (int ks = 0; ks < k.KL16; ++ks) {
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        if (ks >= k.KL16) break;
         uint32_t ah[4], am[4], al[4];
         const size_t at = (size_t)(16 * ks + r + 8 * (j >> 1)) * kXS + 16 * warp + 8 * (j & 1);
         ldsm_x4_t(smem_addr(xt + at), ah[0], ah[1], ah[2], ah[3]);
