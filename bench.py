@@ -13,8 +13,8 @@ B*C_in*Nx*Ny*Nz*Nt per step / step time).
 
 The headline precision is split BF16 (bf16x3: DFT contractions on the tensor
 cores as hi.hi + hi.lo + lo.hi products, FP32 accumulation).  After the timed
-region the same inputs are run in FP32 (plain form) and BF16 as well; the line
-carries their step times and the rel-L2 of every result against FP32.
+region the same inputs are run in FP32 (plain form), TF32 and BF16 as well; the
+line carries their step times and the rel-L2 of every result against FP32.
 
 --impl reference times the FP64 CPU oracle (the baseline arm) on a bounded
 sample of the same workload (fewer channels), on the host cores.
@@ -203,7 +203,7 @@ def precision_sweep(args, step_of, outs, stream, barrier, units):
     ref_prec = "fp32"
     runs = {}
     ref = None
-    for prec in ["fp32", "bf16", "bf16x3"]:
+    for prec in ["fp32", "tf32", "bf16", "bf16x3"]:
         st = step_of(prec)
         for _ in range(3):
             st()
@@ -227,7 +227,7 @@ def precision_sweep(args, step_of, outs, stream, barrier, units):
                       "rel_l2_vs_fp32": err}
         del res
     runs["note"] = ("FP32 plain form vs the FP64 oracle: rel-L2 ~1e-7 in the parity tests; "
-                    "tolerances vs the oracle: fp32 and bf16x3 1e-5, bf16 2e-2")
+                    "tolerances vs the oracle: fp32 and bf16x3 1e-5, tf32 5e-3, bf16 2e-2")
     return runs
 
 
@@ -308,7 +308,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16", "bf16x3"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -356,7 +356,7 @@ def main():
     d = ops.dims_of(x, C, modes)
     p = ops.precision_code(args.precision)
     nws = max(_lib.fno_workspace_bytes(d, ops.precision_code(q), op)
-              for q in ("fp32", "bf16", "bf16x3") for op in (ops.OP_BLOCK_FWD, ops.OP_BLOCK_BWD))
+              for q in ("fp32", "tf32", "bf16", "bf16x3") for op in (ops.OP_BLOCK_FWD, ops.OP_BLOCK_BWD))
     ws = torch.empty(nws, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = int(stream.cuda_stream)
@@ -458,7 +458,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32",
                                            "bf16x3": "bf16x3+f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "B": B, "C_in": C, "C_out": C,

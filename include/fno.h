@@ -56,11 +56,19 @@ typedef struct fno_dims {
   int64_t B, C_in, C_out, Nx, Ny, Nz, Nt, mx, my, mz, mt;
 } fno_dims;
 
-/* Arithmetic of the DFT contractions (accumulation is always FP32):
+/* Arithmetic of the contractions (accumulation is always FP32):
  *   FNO_FP32    FP32 on the CUDA cores (the plain form)
- *   FNO_TF32    TF32 tensor-core products
- *   FNO_BF16    BF16 tensor-core products
- *   FNO_BF16X3  split BF16 (hi + lo, three products) on the tensor cores   */
+ *   FNO_TF32    TF32 numerics: every tensor-core operand rounded to TF32
+ *               (nearest), exact products; a TF32 value is exact as BF16
+ *               hi + lo, so it runs as split products on the BF16 tensor
+ *               cores (the cost of FNO_BF16X3, the accuracy of TF32)
+ *   FNO_BF16    BF16 tensor-core products (one product)
+ *   FNO_BF16X3  split BF16 on the tensor cores: hi + lo with three products
+ *               in the DFT stages, three-way splits with six products in the
+ *               1x1 and line stages
+ * The tensor-core precisions need Nz in {16, 32, 64, 128}, Nt a multiple of 8
+ * up to 64 and mt <= 8 (FNO_ERR_UNSUPPORTED otherwise); stages outside the
+ * tensor-core tilings fall back to the FP32 kernels. */
 typedef enum fno_precision {
   FNO_FP32 = 0,
   FNO_TF32 = 1,

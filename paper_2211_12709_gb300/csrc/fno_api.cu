@@ -123,14 +123,18 @@ static int to_dims(const fno_dims* dd, Dims* d) {
   return FNO_OK;
 }
 
+static bool is_tc(int precision) {
+  return precision == FNO_BF16 || precision == FNO_BF16X3 || precision == FNO_TF32;
+}
+// split operands (hi + lo): split BF16, and TF32 (a TF32 value is exact in two BF16 parts)
+static bool is_split(int precision) { return precision == FNO_BF16X3 || precision == FNO_TF32; }
+
 static int check_support(const Dims& d, int precision, int op) {
   if (precision < FNO_FP32 || precision > FNO_BF16X3)
     return fail(FNO_ERR_INVALID_ARG, "precision %d is not an fno_precision", precision);
   if (op < FNO_OP_SPECTRAL_FWD || op > FNO_OP_BLOCK_BWD)
     return fail(FNO_ERR_INVALID_ARG, "op %d is not an fno_op", op);
-  if (precision == FNO_TF32)
-    return fail(FNO_ERR_UNSUPPORTED, "precision FNO_TF32 is not available in this build");
-  if (precision == FNO_BF16 || precision == FNO_BF16X3) {
+  if (is_tc(precision)) {
     char why[256];
     if (!fwd_tz_tc_supported(d, why, sizeof(why))) return fail(FNO_ERR_UNSUPPORTED, "%s", why);
   }
@@ -231,13 +235,12 @@ static int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
   } while (0)
 
-static bool is_tc(int precision) { return precision == FNO_BF16 || precision == FNO_BF16X3; }
 
 // One complex axis: mma.sync for the tensor-core precisions, FP32 otherwise.
 static cudaError_t line(const float2* in, float2* out, int64_t outer, int nin, int nout, int64_t inner,
                         const float2* tab, int precision, cudaStream_t s) {
   if (is_tc(precision) && line_mma_supported(nin, nout))
-    return launch_line_mma(in, out, outer, nin, nout, inner, tab, precision == FNO_BF16X3, s);
+    return launch_line_mma(in, out, outer, nin, nout, inner, tab, is_split(precision), precision == FNO_TF32, s);
   return launch_line_f32(in, out, outer, nin, nout, inner, tab, s);
 }
 
@@ -247,7 +250,8 @@ static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2
                         const Tables& T, float2* t1, float2* t2, float2* out, cudaStream_t s,
                         int precision = FNO_FP32, int* err = nullptr) {
   if (is_tc(precision))
-    CK(launch_fwd_tz_tc(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, precision == FNO_BF16X3, err, s));
+    CK(launch_fwd_tz_tc(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, is_split(precision), precision == FNO_TF32,
+                        err, s));
   else
     CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
   CK(line(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, precision, s));
@@ -269,7 +273,8 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
 static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base, const Layout& L,
                             int* err, int* grid_used, cudaStream_t s) {
   if (is_tc(precision) && epilogue_mma_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
-    return launch_epilogue_mma(d, a, precision == FNO_BF16X3, base + L.mma_tab, err, grid_used, s);
+    return launch_epilogue_mma(d, a, is_split(precision), precision == FNO_TF32, base + L.mma_tab, err,
+                               grid_used, s);
   return launch_epilogue_f32(d, a, grid_used, s);
 }
 

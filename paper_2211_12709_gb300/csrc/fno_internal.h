@@ -89,21 +89,22 @@ cudaError_t launch_fill_zero(float* p, int64_t n, cudaStream_t s);
 // epilogue_mma_table_bytes(d) for the basis fragments.
 bool epilogue_mma_supported(const Dims& d, int mode, int Cs, int Cl, char* why, size_t nwhy);
 size_t epilogue_mma_table_bytes(const Dims& d);
-cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, void* table, int* err,
-                                int* grid_used, cudaStream_t s);
+cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, bool tf32, void* table,
+                                int* err, int* grid_used, cudaStream_t s);
 
-// One complex DFT axis on mma.sync (fno_mma.cu), BF16 (one product) or split
-// BF16 (three-way splits, six products); same contract as launch_line_f32.
+// One complex DFT axis on mma.sync (fno_mma.cu), BF16 (one product), split
+// BF16 (three-way splits, six products) or TF32 (operands rounded to TF32, then
+// split); same contract as launch_line_f32.
 bool line_mma_supported(int nin, int nout);
 cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int nin, int nout,
-                            int64_t inner, const float2* tab, bool split, cudaStream_t s);
+                            int64_t inner, const float2* tab, bool split, bool tf32, cudaStream_t s);
 
 // ---- tensor-core path (fno_tc.cu) -------------------------------------------
 // Pruned DFT over t then z on tcgen05 (BF16 or split BF16); same contract as
 // launch_fwd_tz_f32.  err: device word set to nonzero when a bounded wait gives up.
 bool fwd_tz_tc_supported(const Dims& d, char* why, size_t nwhy);
 cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const Dims& d,
-                             const float2* ft, const float2* fz, bool split, int* err,
+                             const float2* ft, const float2* fz, bool split, bool tf32, int* err,
                              cudaStream_t s);
 
 #ifdef __CUDACC__

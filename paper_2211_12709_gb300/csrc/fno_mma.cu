@@ -120,6 +120,18 @@ __device__ __forceinline__ void stsm_x2_t(uint32_t a, uint32_t r0, uint32_t r1) 
                : "memory");
 }
 
+// Round to TF32 (10 stored mantissa bits, nearest, ties away).  A TF32 value is
+// exact as BF16 hi + lo, so split products of rounded operands are TF32 products.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+template <bool TF>
+__device__ __forceinline__ float rnd(float x) {
+  return TF ? tf32_round(x) : x;
+}
+
 // three-way BF16 split of two floats: a = h + m + l exactly (FP32 inputs)
 __device__ __forceinline__ void split3(float a, float b, uint32_t& h, uint32_t& m, uint32_t& l) {
   const __nv_bfloat162 hv = __floats2bfloat162_rn(a, b);
@@ -260,7 +272,7 @@ static void epi_mma_geometry(const Dims& d, int mode, int Cs, int Cl, bool split
 //   part 0: B[(jz, 0)] = Re Iz, B[(jz, 1)] = -Im Iz
 //   part 1: B[(jz, 0)] = Im Iz, B[(jz, 1)] =  Re Iz
 // ---------------------------------------------------------------------------
-__global__ void k_epi_mma_bz(const float2* __restrict__ Iz, int Nz, int Jz, int KZ,
+__global__ void k_epi_mma_bz(const float2* __restrict__ Iz, int Nz, int Jz, int KZ, int tf32,
                              uint2* __restrict__ bz) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int total = (Nz / 4) * KZ * 32;
@@ -271,8 +283,8 @@ __global__ void k_epi_mma_bz(const float2* __restrict__ Iz, int Nz, int Jz, int 
     const int jz = kk / 2, kp = kk % 2;
     if (jz >= Jz) return 0.f;
     const float2 f = Iz[(size_t)z * Jz + jz];
-    if (part == 0) return kp == 0 ? f.x : -f.y;
-    return kp == 0 ? f.y : f.x;
+    const float v = (part == 0) ? (kp == 0 ? f.x : -f.y) : (kp == 0 ? f.y : f.x);
+    return tf32 ? tf32_round(v) : v;
   };
   const int k0 = 16 * ks + 2 * (lane % 4);
   uint32_t h0, l0, h1, l1;
@@ -284,7 +296,7 @@ __global__ void k_epi_mma_bz(const float2* __restrict__ Iz, int Nz, int Jz, int 
 }
 
 
-template <int MODE, bool SPLIT>
+template <int MODE, bool SPLIT, bool TF>
 __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__ EpiM k) {
   extern __shared__ __align__(128) unsigned char smem[];
   const EpiArgs& a = k.a;
@@ -335,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
         const int jt = k2 & 7;
         if (jt >= k.Jt) return 0.f;
         const float2 f = a.It[(size_t)jt * Nt + t];
-        return k2 < 8 ? f.x : -f.y;
+        return rnd<TF>(k2 < 8 ? f.x : -f.y);
       };
       const int t0 = 16 * mt + ln / 4, c0 = 2 * (ln % 4);
       uint4 h, l;
@@ -354,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
       const int ln = e % 32, nt = (e / 32) % kNTM, ks = e / (32 * kNTM);
       const int o = 8 * nt + ln / 4;
       auto W = [&](int i) -> float {
-        return (i < Cl && o < Cs) ? a.wlin[(size_t)i * a.w_si + (size_t)o * a.w_sc] : 0.f;
+        return (i < Cl && o < Cs) ? rnd<TF>(a.wlin[(size_t)i * a.w_si + (size_t)o * a.w_sc]) : 0.f;
       };
       const int i0 = 16 * ks + 2 * (ln % 4);
       uint2 h, m, l;
@@ -433,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
         const int o = e / JZT, r = e - o * JZT, jz = r / k.Jt, jt = r - jz * k.Jt;
         const float2 u = __ldg(U + (size_t)o * k.NxNy * JZT + r);
         uint32_t h, l;
-        split2(u.x, u.y, h, l);
+        split2(rnd<TF>(u.x), rnd<TF>(u.y), h, l);
         const size_t at = (size_t)(o * 8 + jt) * UK + 2 * jz;
         *reinterpret_cast<uint32_t*>(u_hi + at) = h;
         *reinterpret_cast<uint32_t*>(u_lo + at) = l;
@@ -531,12 +543,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
             const int o = 2 * m1 + (j & 1), ntz = (k.NZT == 2) ? (j >> 1) : 0;
             const size_t at = (size_t)(4 * ntz + (r >> 1)) * QP + (size_t)o * 24 + 8 * (r & 1);
             uint32_t h0, l0, h1, l1;
-            split2(cc[0][0], cc[0][1], h0, l0);  // (o_a, planes 0-3)
-            split2(cc[0][2], cc[0][3], h1, l1);  // (o_b, planes 0-3)
+            split2(rnd<TF>(cc[0][0]), rnd<TF>(cc[0][1]), h0, l0);  // (o_a, planes 0-3)
+            split2(rnd<TF>(cc[0][2]), rnd<TF>(cc[0][3]), h1, l1);  // (o_b, planes 0-3)
             if (k.NZT == 2) {
               uint32_t h2, l2, h3, l3;
-              split2(cc[1][0], cc[1][1], h2, l2);  // (o_a, planes 4-7)
-              split2(cc[1][2], cc[1][3], h3, l3);  // (o_b, planes 4-7)
+              split2(rnd<TF>(cc[1][0]), rnd<TF>(cc[1][1]), h2, l2);  // (o_a, planes 4-7)
+              split2(rnd<TF>(cc[1][2]), rnd<TF>(cc[1][3]), h3, l3);  // (o_b, planes 4-7)
               stsm_x4_t(smem_addr(q_hi + at), h0, h1, h2, h3);
               stsm_x4_t(smem_addr(q_lo + at), l0, l1, l2, l3);
             } else {
@@ -557,8 +569,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
         const size_t at = (size_t)i * kXS + p4;
         if (SPLIT) {
           uint2 h, m, l;
-          split3(v.x, v.y, h.x, m.x, l.x);
-          split3(v.z, v.w, h.y, m.y, l.y);
+          split3(rnd<TF>(v.x), rnd<TF>(v.y), h.x, m.x, l.x);
+          split3(rnd<TF>(v.z), rnd<TF>(v.w), h.y, m.y, l.y);
           *reinterpret_cast<uint2*>(xt + at) = h;
           *reinterpret_cast<uint2*>(xt + XP + at) = m;
           *reinterpret_cast<uint2*>(xt + 2 * XP + at) = l;
@@ -709,8 +721,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
             const size_t at = (size_t)(8 * nt + r) * kXS + 16 * warp + 8 * j;
             if (SPLIT) {
               uint32_t h0, m0, l0, h1, m1_, l1;
-              split3(acc[nt][0], acc[nt][1], h0, m0, l0);
-              split3(acc[nt][2], acc[nt][3], h1, m1_, l1);
+              split3(rnd<TF>(acc[nt][0]), rnd<TF>(acc[nt][1]), h0, m0, l0);
+              split3(rnd<TF>(acc[nt][2]), rnd<TF>(acc[nt][3]), h1, m1_, l1);
               stsm_x2_t(smem_addr(dt + at), h0, h1);
               stsm_x2_t(smem_addr(dt + DP + at), m0, m1_);
               stsm_x2_t(smem_addr(dt + 2 * DP + at), l0, l1);
@@ -842,9 +854,9 @@ bool epilogue_mma_supported(const Dims& d, int mode, int Cs, int Cl, char* why, 
   return true;
 }
 
-template <int MODE, bool SPLIT>
+template <int MODE, bool SPLIT, bool TF>
 static cudaError_t launch_mma_t(const EpiM& k, int* grid_used, cudaStream_t s) {
-  const void* kern = (const void*)k_epi_mma<MODE, SPLIT>;
+  const void* kern = (const void*)k_epi_mma<MODE, SPLIT, TF>;
   const size_t smem = k.off[R_END];
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -857,17 +869,19 @@ static cudaError_t launch_mma_t(const EpiM& k, int* grid_used, cudaStream_t s) {
   if (g > epilogue_max_grid()) g = epilogue_max_grid();
   if (g < 1) g = 1;
   if (grid_used) *grid_used = (int)g;
-  static const char* names[2][4] = {
+  static const char* names[3][4] = {
       {"fno_epi_spectral_mma_bf16", "fno_epi_fwd_mma_bf16", "fno_epi_da_mma_bf16", "fno_epi_dx_mma_bf16"},
       {"fno_epi_spectral_mma_bf16x3", "fno_epi_fwd_mma_bf16x3", "fno_epi_da_mma_bf16x3",
-       "fno_epi_dx_mma_bf16x3"}};
-  FNO_LAUNCH(names[SPLIT ? 1 : 0][MODE], (k_epi_mma<MODE, SPLIT>), (int)g, kThreads, smem, s, k);
+       "fno_epi_dx_mma_bf16x3"},
+      {"fno_epi_spectral_mma_tf32", "fno_epi_fwd_mma_tf32", "fno_epi_da_mma_tf32", "fno_epi_dx_mma_tf32"}};
+  FNO_LAUNCH(names[TF ? 2 : (SPLIT ? 1 : 0)][MODE], (k_epi_mma<MODE, SPLIT, TF>), (int)g, kThreads, smem, s, k);
   return cudaSuccess;
 }
 
 template <int MODE>
-static cudaError_t launch_mma_m(const EpiM& k, bool split, int* g, cudaStream_t s) {
-  return split ? launch_mma_t<MODE, true>(k, g, s) : launch_mma_t<MODE, false>(k, g, s);
+static cudaError_t launch_mma_m(const EpiM& k, bool split, bool tf32, int* g, cudaStream_t s) {
+  if (tf32) return launch_mma_t<MODE, true, true>(k, g, s);
+  return split ? launch_mma_t<MODE, true, false>(k, g, s) : launch_mma_t<MODE, false, false>(k, g, s);
 }
 
 // Tensor map of a [rows][chan] FP32 array with boxes of box_rows x 128 points,
@@ -898,8 +912,8 @@ static cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long c
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, void* table, int* err,
-                                int* grid_used, cudaStream_t s) {
+cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, bool tf32, void* table,
+                                int* err, int* grid_used, cudaStream_t s) {
   EpiM k{};
   k.a = a;
   k.err = err;
@@ -917,13 +931,13 @@ cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, voi
   {
     const int total = (k.Nz / 4) * k.KZ * 32;
     FNO_LAUNCH("fno_epi_mma_tables", k_epi_mma_bz, (total + 255) / 256, 256, 0, s, a.Iz, k.Nz,
-               k.Jz, k.KZ, bz);
+               k.Jz, k.KZ, tf32 ? 1 : 0, bz);
   }
   switch (a.mode) {
-    case EPI_SPECTRAL: return launch_mma_m<EPI_SPECTRAL>(k, split, grid_used, s);
-    case EPI_FWD: return launch_mma_m<EPI_FWD>(k, split, grid_used, s);
-    case EPI_DA: return launch_mma_m<EPI_DA>(k, split, grid_used, s);
-    default: return launch_mma_m<EPI_DX>(k, split, grid_used, s);
+    case EPI_SPECTRAL: return launch_mma_m<EPI_SPECTRAL>(k, split, tf32, grid_used, s);
+    case EPI_FWD: return launch_mma_m<EPI_FWD>(k, split, tf32, grid_used, s);
+    case EPI_DA: return launch_mma_m<EPI_DA>(k, split, tf32, grid_used, s);
+    default: return launch_mma_m<EPI_DX>(k, split, tf32, grid_used, s);
   }
 }
 
@@ -954,7 +968,7 @@ struct LineM {
 constexpr int kLineMTMax = 4;  // m-tiles held at once when streaming K
 constexpr int kLineKSMax = 4;  // k-steps held at once when walking m-tiles
 
-template <bool SPLIT, bool KOUTER>
+template <bool SPLIT, bool KOUTER, bool TF>
 __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint4* af = reinterpret_cast<uint4*>(smem);  // [MT][KS][parts][32 lanes]
@@ -970,8 +984,7 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
       const int q = m >> 1, po = m & 1, n = kk >> 1, pi = kk & 1;
       if (q >= nout || n >= nin) return 0.f;
       const float2 t = L.tab[(size_t)q * nin + n];
-      if (po == 0) return pi == 0 ? t.x : -t.y;
-      return pi == 0 ? t.y : t.x;
+      return rnd<TF>((po == 0) ? (pi == 0 ? t.x : -t.y) : (pi == 0 ? t.y : t.x));
     };
     const int r0 = 16 * mt + ln / 4, c0 = 16 * ks + 2 * (ln % 4);
     uint4 h, m, l;
@@ -1005,6 +1018,8 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
           const int n = 8 * ks + 4 * hf + t4;
           float2 v = make_float2(0.f, 0.f);
           if (n < nin && col < L.inner) v = __ldg(src + (size_t)n * L.inner + col);
+          v.x = rnd<TF>(v.x);
+          v.y = rnd<TF>(v.y);
           if (SPLIT)
             split3(v.x, v.y, bh[nt][hf], bm[nt][hf], bl[nt][hf]);
           else {
@@ -1052,6 +1067,8 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+      // the tensor-core FP32 accumulation is not round-to-nearest, so each
+      // k-step accumulates from zero and is added into the total in FP32
       for (int ks = 0; ks < KS; ++ks) {
         uint32_t bh[2][2], bm[2][2], bl[2][2];
         loadB(ks, bh, bm, bl);
@@ -1060,7 +1077,12 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
           if (mt < MT) {
             const uint4* a = af + ((size_t)(mt * KS + ks) * NP) * 32 + lane;
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) mma_parts(acc[mt][nt], a, bh[nt], bm[nt], bl[nt]);
+            for (int nt = 0; nt < 2; ++nt) {
+              float part[4] = {0.f, 0.f, 0.f, 0.f};
+              mma_parts(part, a, bh[nt], bm[nt], bl[nt]);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[mt][nt][q] += part[q];
+            }
           }
       }
 #pragma unroll
@@ -1085,7 +1107,12 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
           if (ks < KS) {
             const uint4* a = af + ((size_t)(mt * KS + ks) * NP) * 32 + lane;
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) mma_parts(acc[nt], a, bh[ks][nt], bm[ks][nt], bl[ks][nt]);
+            for (int nt = 0; nt < 2; ++nt) {
+              float part[4] = {0.f, 0.f, 0.f, 0.f};
+              mma_parts(part, a, bh[ks][nt], bm[ks][nt], bl[ks][nt]);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[nt][q] += part[q];
+            }
           }
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) store(mt, nt, acc[nt]);
@@ -1099,8 +1126,24 @@ bool line_mma_supported(int nin, int nout) {
   return MT <= kLineMTMax || KS <= kLineKSMax;
 }
 
+template <bool SPLIT, bool KOUTER, bool TF>
+static cudaError_t launch_line_t(const LineM& L, size_t smem, const char* name, cudaStream_t s) {
+  const void* kern = (const void*)k_line_mma<SPLIT, KOUTER, TF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long tasks = L.outer * L.ncb;
+  long long g = (long long)per_sm * sm_count();
+  if (g * 8 > tasks) g = (tasks + 7) / 8;
+  if (g < 1) g = 1;
+  FNO_LAUNCH(name, (k_line_mma<SPLIT, KOUTER, TF>), (int)g, 256, smem, s, L);
+  return cudaSuccess;
+}
+
 cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int nin, int nout,
-                            int64_t inner, const float2* tab, bool split, cudaStream_t s) {
+                            int64_t inner, const float2* tab, bool split, bool tf32, cudaStream_t s) {
   if (outer <= 0 || inner <= 0) return cudaSuccess;
   LineM L{};
   L.in = in;
@@ -1115,31 +1158,16 @@ cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int ni
   L.KS = (2 * nin + 15) / 16;
   const bool kouter = L.MT <= kLineMTMax;
   if (!kouter && L.KS > kLineKSMax) return cudaErrorInvalidValue;
+  split = split || tf32;
   const size_t smem = sizeof(uint4) * (size_t)L.MT * L.KS * (split ? 3 : 1) * 32;
-  const void* kern = split ? (kouter ? (const void*)k_line_mma<true, true> : (const void*)k_line_mma<true, false>)
-                           : (kouter ? (const void*)k_line_mma<false, true> : (const void*)k_line_mma<false, false>);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  const long long tasks = outer * L.ncb;
-  long long g = (long long)per_sm * sm_count();
-  if (g * 8 > tasks) g = (tasks + 7) / 8;
-  if (g < 1) g = 1;
-  const char* name = split ? "fno_line_mma_bf16x3" : "fno_line_mma_bf16";
-  if (split) {
-    if (kouter)
-      FNO_LAUNCH(name, (k_line_mma<true, true>), (int)g, 256, smem, s, L);
-    else
-      FNO_LAUNCH(name, (k_line_mma<true, false>), (int)g, 256, smem, s, L);
-  } else {
-    if (kouter)
-      FNO_LAUNCH(name, (k_line_mma<false, true>), (int)g, 256, smem, s, L);
-    else
-      FNO_LAUNCH(name, (k_line_mma<false, false>), (int)g, 256, smem, s, L);
-  }
-  return cudaSuccess;
+  if (tf32)
+    return kouter ? launch_line_t<true, true, true>(L, smem, "fno_line_mma_tf32", s)
+                  : launch_line_t<true, false, true>(L, smem, "fno_line_mma_tf32", s);
+  if (split)
+    return kouter ? launch_line_t<true, true, false>(L, smem, "fno_line_mma_bf16x3", s)
+                  : launch_line_t<true, false, false>(L, smem, "fno_line_mma_bf16x3", s);
+  return kouter ? launch_line_t<false, true, false>(L, smem, "fno_line_mma_bf16", s)
+                : launch_line_t<false, false, false>(L, smem, "fno_line_mma_bf16", s);
 }
 
 }  // namespace fno

@@ -43,6 +43,17 @@ __device__ __forceinline__ void split1(float a, __nv_bfloat16& hi, __nv_bfloat16
   hi = __float2bfloat16_rn(a);
   lo = __float2bfloat16_rn(a - __bfloat162float(hi));
 }
+// Round to TF32 (10 stored mantissa bits, nearest, ties away); a TF32 value is
+// exact as BF16 hi + lo, so the split products reproduce TF32 arithmetic.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+template <bool TF>
+__device__ __forceinline__ float rnd(float x) {
+  return TF ? tf32_round(x) : x;
+}
 // byte offset of element (r, k) of a 2-byte K-major no-swizzle operand
 __device__ __forceinline__ uint32_t koff(uint32_t r, uint32_t k, uint32_t sbo, uint32_t lbo) {
   return (r & 7u) * 16u + (r >> 3) * sbo + (k & 7u) * 2u + (k >> 3) * lbo;
@@ -114,7 +125,7 @@ __device__ __forceinline__ void mma_sync16(float (&d)[4], uint32_t a0, uint32_t 
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <bool SPLIT>
+template <bool SPLIT, bool TF>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_tz_tc(const FwdTcK p) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -160,7 +171,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_tz_tc(const FwdTcK p) {
       v = (n & 1) ? f.y : f.x;
     }
     __nv_bfloat16 h, l;
-    split1(v, h, l);
+    split1(rnd<TF>(v), h, l);
     const uint32_t off = koff(n, z, sbo_b2, 128);
     *reinterpret_cast<__nv_bfloat16*>(b2 + off) = h;
     *reinterpret_cast<__nv_bfloat16*>(b2 + p.b2_bytes + off) = l;
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_tz_tc(const FwdTcK p) {
         auto F = [&](int t) -> float {
           if (g8 >= Jt || t >= Nt) return 0.f;
           const float2 f = p.Ft[g8 * Nt + t];
-          return ri ? f.y : f.x;
+          return rnd<TF>(ri ? f.y : f.x);
         };
         const int t0 = 16 * ks + 4 * t4;
         split2(F(t0), F(t0 + 1), bfh[ri][ks][0], bfl[ri][ks][0]);
@@ -293,10 +304,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_tz_tc(const FwdTcK p) {
                 if (r1 < rows) v1 = *reinterpret_cast<const float4*>(xs + r1 * Nt + tt);
               }
               uint32_t ah[4], al[4];
-              split2(v0.x, v0.y, ah[0], al[0]);
-              split2(v1.x, v1.y, ah[1], al[1]);
-              split2(v0.z, v0.w, ah[2], al[2]);
-              split2(v1.z, v1.w, ah[3], al[3]);
+              split2(rnd<TF>(v0.x), rnd<TF>(v0.y), ah[0], al[0]);
+              split2(rnd<TF>(v1.x), rnd<TF>(v1.y), ah[1], al[1]);
+              split2(rnd<TF>(v0.z), rnd<TF>(v0.w), ah[2], al[2]);
+              split2(rnd<TF>(v1.z), rnd<TF>(v1.w), ah[3], al[3]);
               if (SPLIT) {
 #pragma unroll
                 for (int ri = 0; ri < 2; ++ri)
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_tz_tc(const FwdTcK p) {
               const int row = h2 ? r1 : r0;
               const int cl = j * p.cpt + row / Nz, z = row % Nz;
               uint32_t hv, lv;
-              split2(acc[ri][2 * h2], acc[ri][2 * h2 + 1], hv, lv);
+              split2(rnd<TF>(acc[ri][2 * h2]), rnd<TF>(acc[ri][2 * h2 + 1]), hv, lv);
               const uint32_t off = (uint32_t)(cl * 2 + ri) * 128u + 4u * (uint32_t)t4 +
                                    (uint32_t)(z & 7) * 16u + (uint32_t)(z >> 3) * kg_a2;
               *reinterpret_cast<uint32_t*>(ah2 + off) = hv;
@@ -433,12 +444,12 @@ bool fwd_tz_tc_supported(const Dims& d, char* why, size_t nwhy) {
 }
 
 cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const Dims& d,
-                             const float2* ft, const float2* fz, bool split, int* err,
+                             const float2* ft, const float2* fz, bool split, bool tf32, int* err,
                              cudaStream_t s) {
   if (ncol <= 0) return cudaSuccess;
   FwdTcK k{};
   size_t smem = 0;
-  if (!fwd_tz_plan(d, split, k, smem, nullptr, 0)) return cudaErrorInvalidValue;
+  if (!fwd_tz_plan(d, split || tf32, k, smem, nullptr, 0)) return cudaErrorInvalidValue;
   k.in = in;
   k.out = out;
   k.Ft = ft;
@@ -446,14 +457,17 @@ cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const D
   k.err = err;
   k.ncol = ncol;
   k.ngroups = (ncol + kG - 1) / kG;
-  const void* kern = split ? (const void*)k_fwd_tz_tc<true> : (const void*)k_fwd_tz_tc<false>;
+  const void* kern = tf32 ? (const void*)k_fwd_tz_tc<true, true>
+                          : (split ? (const void*)k_fwd_tz_tc<true, false> : (const void*)k_fwd_tz_tc<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(k.ngroups, sm_count());
-  if (split)
-    FNO_LAUNCH("fno_fwd_tz_tc_bf16x3", k_fwd_tz_tc<true>, grid, kFwdThreads, smem, s, k);
+  if (tf32)
+    FNO_LAUNCH("fno_fwd_tz_tc_tf32", (k_fwd_tz_tc<true, true>), grid, kFwdThreads, smem, s, k);
+  else if (split)
+    FNO_LAUNCH("fno_fwd_tz_tc_bf16x3", (k_fwd_tz_tc<true, false>), grid, kFwdThreads, smem, s, k);
   else
-    FNO_LAUNCH("fno_fwd_tz_tc_bf16", k_fwd_tz_tc<false>, grid, kFwdThreads, smem, s, k);
+    FNO_LAUNCH("fno_fwd_tz_tc_bf16", (k_fwd_tz_tc<false, false>), grid, kFwdThreads, smem, s, k);
   return cudaSuccess;
 }
 
