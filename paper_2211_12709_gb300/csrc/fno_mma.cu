@@ -420,11 +420,72 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
 #pragma unroll
     for (int q = 0; q < 4; ++q) ks_sum[u][q] = ks_cmp[u][q] = 0.f;
 
+  // stage 5 (dA mode): dW_lin and db over the 128 points of the tile whose x
+  // and dA tiles are in shared memory, Kahan-folded into this warp's units
+  auto stage5 = [&]() {
+#pragma unroll
+    for (int ui = 0; ui < 2; ++ui) {
+      const int u = warp + ui * kWarps;
+      if (u < k.nunits) {
+        const int mi = u / NT, nt = u - mi * NT;
+        // four dependency chains: k-step parity x (large, small) products
+        float c5[2][2][4];
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int y = 0; y < 2; ++y)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c5[x][y][q] = 0.f;
+        const int row = min(16 * mi + (lane & 7) + 8 * ((lane >> 3) & 1), k.XR - 1);
+        const int j = lane >> 3, r = lane & 7;
+#pragma unroll 2
+        for (int ks = 0; ks < kP / 16; ++ks) {
+          float(&cl)[4] = c5[ks & 1][0];
+          float(&cs)[4] = c5[ks & 1][1];
+          uint32_t ah[4], am[4], al[4];
+          const size_t ax = (size_t)row * kXS + 16 * ks + 8 * (lane >> 4);
+          const size_t bx = (size_t)(8 * nt + r) * kXS + 16 * ks + 8 * (j & 1);
+          ldsm_x4(smem_addr(xt + ax), ah[0], ah[1], ah[2], ah[3]);
+          if (SPLIT) {
+            ldsm_x4(smem_addr(xt + XP + ax), am[0], am[1], am[2], am[3]);
+            ldsm_x4(smem_addr(xt + 2 * XP + ax), al[0], al[1], al[2], al[3]);
+            uint2 bh, bm, bl;
+            ldsm_x4(smem_addr(dt + ((j >> 1) ? DP : 0) + bx), bh.x, bh.y, bm.x, bm.y);
+            ldsm_x2(smem_addr(dt + 2 * DP + bx), bl.x, bl.y);
+            mma16(cs, am[0], am[1], am[2], am[3], bm.x, bm.y);
+            mma16(cl, am[0], am[1], am[2], am[3], bh.x, bh.y);
+            mma16(cs, al[0], al[1], al[2], al[3], bh.x, bh.y);
+            mma16(cl, ah[0], ah[1], ah[2], ah[3], bm.x, bm.y);
+            mma16(cs, ah[0], ah[1], ah[2], ah[3], bl.x, bl.y);
+            mma16(cl, ah[0], ah[1], ah[2], ah[3], bh.x, bh.y);
+          } else {
+            uint32_t b0, b1;
+            ldsm_x2(smem_addr(dt + bx), b0, b1);
+            mma16(cl, ah[0], ah[1], ah[2], ah[3], b0, b1);
+          }
+        }
+        float c5s[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          c5s[q] = (c5[0][1][q] + c5[1][1][q]) + (c5[0][0][q] + c5[1][0][q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float y = c5s[q] - ks_cmp[ui][q];
+          const float t = ks_sum[ui][q] + y;
+          ks_cmp[ui][q] = (t - ks_sum[ui][q]) - y;
+          ks_sum[ui][q] = t;
+        }
+      }
+    }
+  };
+
+  bool prev_valid = false;
   for (long long tau = t_begin, c = 0; tau < t_end; ++tau, ++c) {
     const long long tile_ofs = xy * k.plane + (long long)zb * kP;
     const int buf = (int)(c & 1);
-    __syncthreads();  // S0: every shared-memory read of the previous tile is done
-    if (s_abort) break;
+    // S0: every shared-memory read of the previous tile is done; the abort
+    // decision is the OR over the CTA, so every thread takes the same branch
+    if (__syncthreads_or(s_abort != 0)) break;
     // the next tile (prefetch its x tile into the other buffer)
     int zbn = zb + 1;
     long long xyn = xy, bn = b;
@@ -478,11 +539,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
     const uint2* bzs = reinterpret_cast<const uint2*>(sgb + k.BZO);
     if (newcol) __syncthreads();  // S1: the rebuilt U' is ready
 
+    // dA mode: stage 5 of the previous tile (its x and dA tiles) beside stage 1
+    if (MODE == EPI_DA && prev_valid) stage5();
+
     // ---- stage 1: inverse z of the tile's planes -> Q (BF16 hi/lo) --------
-    // warp w owns m-tiles w and w + 8 (when M1 > 8); both run interleaved
+    // m-tile k goes to warp (k + nunits) % 8, so the warps without a stage-5
+    // unit take the m-tiles first; a warp owns m-tiles w1 and w1 + 8
     {
-      const bool two = warp + kWarps < k.M1;
-      if (warp < k.M1) {
+      const int w1 = (warp + kWarps - (k.nunits % kWarps)) % kWarps;
+      const bool two = w1 + kWarps < k.M1;
+      if (w1 < k.M1) {
         // c1: hi.hi products; c1s: the cross terms (a second dependency chain)
         float c1[2][2][4], c1s[2][2][4];
 #pragma unroll
@@ -499,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               if (u == 0 || two) {
-                const int row = 16 * (warp + u * kWarps) + (lane & 7) + 8 * ((lane >> 3) & 1);
+                const int row = 16 * (w1 + u * kWarps) + (lane & 7) + 8 * ((lane >> 3) & 1);
                 ldsm_x4(smem_addr(u_hi + (size_t)row * UK + kc), ah[u][0], ah[u][1], ah[u][2], ah[u][3]);
                 if (SPLIT)
                   ldsm_x4(smem_addr(u_lo + (size_t)row * UK + kc), al[u][0], al[u][1], al[u][2], al[u][3]);
@@ -532,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           if (u == 0 || two) {
-            const int m1 = warp + u * kWarps;
+            const int m1 = w1 + u * kWarps;
             float(&cc)[2][4] = c1[u];
 #pragma unroll
             for (int n = 0; n < 2; ++n)
@@ -560,6 +626,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
       }
     }
 
+    // dA mode: stage 5 of the previous tile is done with the x tile
+    if (MODE == EPI_DA) __syncthreads();
     // ---- the x tile: split into BF16 parts ------------------------------------
     if (Cl > 0) {
       const float* sg = reinterpret_cast<const float*>(sgb);
@@ -735,66 +803,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
           }
         }
       }
-      __syncthreads();  // S3: the dA tile is complete
-      // ---- stage 5: dW_lin and db over the tile's 128 points ----------------
-#pragma unroll
-      for (int ui = 0; ui < 2; ++ui) {
-        const int u = warp + ui * kWarps;
-        if (u < k.nunits) {
-          const int mi = u / NT, nt = u - mi * NT;
-          // four dependency chains: k-step parity x (large, small) products
-          float c5[2][2][4];
-#pragma unroll
-          for (int x = 0; x < 2; ++x)
-#pragma unroll
-            for (int y = 0; y < 2; ++y)
-#pragma unroll
-              for (int q = 0; q < 4; ++q) c5[x][y][q] = 0.f;
-          const int row = min(16 * mi + (lane & 7) + 8 * ((lane >> 3) & 1), k.XR - 1);
-          const int j = lane >> 3, r = lane & 7;
-#pragma unroll 2
-          for (int ks = 0; ks < kP / 16; ++ks) {
-            float(&cl)[4] = c5[ks & 1][0];
-            float(&cs)[4] = c5[ks & 1][1];
-            uint32_t ah[4], am[4], al[4];
-            const size_t ax = (size_t)row * kXS + 16 * ks + 8 * (lane >> 4);
-            const size_t bx = (size_t)(8 * nt + r) * kXS + 16 * ks + 8 * (j & 1);
-            ldsm_x4(smem_addr(xt + ax), ah[0], ah[1], ah[2], ah[3]);
-            if (SPLIT) {
-              ldsm_x4(smem_addr(xt + XP + ax), am[0], am[1], am[2], am[3]);
-              ldsm_x4(smem_addr(xt + 2 * XP + ax), al[0], al[1], al[2], al[3]);
-              uint2 bh, bm, bl;
-              ldsm_x4(smem_addr(dt + ((j >> 1) ? DP : 0) + bx), bh.x, bh.y, bm.x, bm.y);
-              ldsm_x2(smem_addr(dt + 2 * DP + bx), bl.x, bl.y);
-              mma16(cs, am[0], am[1], am[2], am[3], bm.x, bm.y);
-              mma16(cl, am[0], am[1], am[2], am[3], bh.x, bh.y);
-              mma16(cs, al[0], al[1], al[2], al[3], bh.x, bh.y);
-              mma16(cl, ah[0], ah[1], ah[2], ah[3], bm.x, bm.y);
-              mma16(cs, ah[0], ah[1], ah[2], ah[3], bl.x, bl.y);
-              mma16(cl, ah[0], ah[1], ah[2], ah[3], bh.x, bh.y);
-            } else {
-              uint32_t b0, b1;
-              ldsm_x2(smem_addr(dt + bx), b0, b1);
-              mma16(cl, ah[0], ah[1], ah[2], ah[3], b0, b1);
-            }
-          }
-          float c5s[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            c5s[q] = (c5[0][1][q] + c5[1][1][q]) + (c5[0][0][q] + c5[1][0][q]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float y = c5s[q] - ks_cmp[ui][q];
-            const float t = ks_sum[ui][q] + y;
-            ks_cmp[ui][q] = (t - ks_sum[ui][q]) - y;
-            ks_sum[ui][q] = t;
-          }
-        }
-      }
     }
+    prev_valid = true;
     b = bn;
     xy = xyn;
     zb = zbn;
+  }
+  // dA mode: stage 5 of the last tile (uniform decision, as at S0)
+  if (MODE == EPI_DA && prev_valid) {
+    if (!__syncthreads_or(s_abort != 0)) stage5();
   }
 
   // bulk copies still in flight after a timed-out wait must land before exit
