@@ -16,10 +16,17 @@ Array conventions (all C-contiguous):
 Stored mode index j < m maps to frequency j, j >= m to j - 2m (x, y, z);
 the t axis keeps kt = 0..mt-1.
 
+The layers around the blocks in Alg. 1 (encoder and decoder pointwise 1x1
+layers with sigma, the mean-squared-error loss) and the composed stack are
+``pointwise_fwd``, ``pointwise_bwd``, ``mse`` and ``stack_loss_and_grads``.
+
 Parity notes: every routine is pinned by the CPU tests in
 ``tests/test_oracle_pins.py`` (brute-force 4-D sums, NumPy ``rfftn``/``irfftn``,
 identity, projector/Parseval, shift equivariance, plane waves, adjoint
-dot-products and central finite differences).
+dot-products and central finite differences) and ``tests/test_oracle_stack_pins.py``
+(the pointwise layers and the loss against PyTorch's CPU ``linear``/``gelu``/
+``mse_loss`` and its autograd, the whole stack against a PyTorch ``rfftn``
+model and against central finite differences).
 """
 from __future__ import annotations
 
@@ -114,6 +121,12 @@ def _bind(lib):
     lib.oracle_block_bwd.argtypes = [_I64P, ci, ci, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp,
                                      vp, vp]
     lib.oracle_block_bwd.restype = ci
+    lib.oracle_pointwise_fwd.argtypes = [i64, i64, i64, i64, ci, ci, vp, vp, vp, vp]
+    lib.oracle_pointwise_fwd.restype = ci
+    lib.oracle_pointwise_bwd.argtypes = [i64, i64, i64, i64, ci, ci, vp, vp, vp, vp, vp, vp, vp]
+    lib.oracle_pointwise_bwd.restype = ci
+    lib.oracle_mse.argtypes = [i64, ci, vp, vp, vp, vp]
+    lib.oracle_mse.restype = ci
     return lib
 
 
@@ -304,3 +317,84 @@ def block_bwd(d: Dims, x, w, dz, wl=None, bias=None, full=True, pts=None):
                                     _ptr(dz), _ptr(dx), npts, _ptr(pp), _ptr(dxp), _ptr(dw),
                                     _ptr(dwl), _ptr(db)), "block_bwd")
     return {"dx": dx, "dx_pts": dxp, "dw": dw, "dwl": dwl, "db": db}
+
+
+# ---------------------------------------------------------------------------
+# Layers around the blocks (Alg. 1) and the composed stack
+# ---------------------------------------------------------------------------
+def pointwise_fwd(x, w, bias=None, act=1):
+    """Y[b,o,p] = sigma(sum_i X[b,i,p] W[i,o] + bias[o]) for x [B, Ci, *grid], w [Ci, Co].
+
+    act 0 = identity, 1 = GELU.  Returns float64 [B, Co, *grid].
+    """
+    dt = _dtype_of(x)
+    x, w, bias = _inputs(dt, x, w, bias)
+    B, Ci = x.shape[:2]
+    grid = x.shape[2:]
+    P = int(np.prod(grid)) if grid else 1
+    Co = w.shape[1]
+    assert w.shape == (Ci, Co), (w.shape, Ci)
+    y = np.empty((B, Co) + tuple(grid), dtype=np.float64)
+    _check(_load().oracle_pointwise_fwd(B, Ci, Co, P, int(act), dt, _ptr(x), _ptr(w), _ptr(bias),
+                                        _ptr(y)), "pointwise_fwd")
+    return y
+
+
+def pointwise_bwd(x, w, dy, bias=None, act=1, need_dx=True):
+    """Gradient of ``pointwise_fwd`` for upstream dy: dict with dx (or None), dw, db."""
+    dt = _dtype_of(x)
+    x, w, bias, dy = _inputs(dt, x, w, bias, dy)
+    B, Ci = x.shape[:2]
+    grid = x.shape[2:]
+    P = int(np.prod(grid)) if grid else 1
+    Co = w.shape[1]
+    assert dy.shape == (B, Co) + tuple(grid), (dy.shape, x.shape, w.shape)
+    dx = np.empty(x.shape, dtype=np.float64) if need_dx else None
+    dw = np.empty((Ci, Co), dtype=np.float64)
+    db = np.empty((Co,), dtype=np.float64)
+    _check(_load().oracle_pointwise_bwd(B, Ci, Co, P, int(act), dt, _ptr(x), _ptr(w), _ptr(bias),
+                                        _ptr(dy), _ptr(dx), _ptr(dw), _ptr(db)), "pointwise_bwd")
+    return {"dx": dx, "dw": dw, "db": db}
+
+
+def mse(y, target):
+    """(L, dL/dy) of L = mean((y - target)^2)."""
+    dt = _dtype_of(y)
+    y, target = _inputs(dt, y, target)
+    assert y.shape == target.shape
+    loss = np.zeros(1, dtype=np.float64)
+    dy = np.empty(y.shape, dtype=np.float64)
+    _check(_load().oracle_mse(y.size, dt, _ptr(y), _ptr(target), _ptr(loss), _ptr(dy)), "mse")
+    return float(loss[0]), dy
+
+
+def stack_loss_and_grads(d: Dims, x0, target, enc, blocks, dec, dec_act=1):
+    """Loss and gradients of the Alg. 1 stack with an MSE loss.
+
+    d: the block sizes (Ci = Co = width).  x0 [B, C0, *grid]; enc = (W_e [C0, width],
+    b_e or None); blocks = [(W [width, width, Jx, Jy, Jz, Jt, 2], W_l, bias), ...];
+    dec = (W_d [width, C_out], b_d or None); target [B, C_out, *grid].
+    Encoder: X1 = GELU(x0 W_e + b_e); block i: X_{i+1} = GELU(S(X_i) + W_l^T X_i + b);
+    decoder: Y = sigma(X W_d + b_d) (sigma = GELU for dec_act 1, identity for 0);
+    L = mean((Y - target)^2).  Returns (L, grads) with grads "x0", "enc" (dw, db),
+    "blocks" [(dw, dwl, db), ...], "dec" (dw, db), and the activations "h" [X1, ...].
+    """
+    assert d.Ci == d.Co
+    h = [pointwise_fwd(x0, enc[0], enc[1], act=1)]
+    for (w, wl, b) in blocks:
+        z, _ = block_fwd(d, h[-1], w, wl, b)
+        h.append(z)
+    y = pointwise_fwd(h[-1], dec[0], dec[1], act=dec_act)
+    loss, dy = mse(y, target)
+    gd = pointwise_bwd(h[-1], dec[0], dy, dec[1], act=dec_act)
+    dh = gd["dx"]
+    gblocks = []
+    for k in range(len(blocks) - 1, -1, -1):
+        w, wl, b = blocks[k]
+        r = block_bwd(d, h[k], w, dh, wl, b)
+        gblocks.append((r["dw"], r["dwl"], r["db"]))
+        dh = r["dx"]
+    gblocks.reverse()
+    ge = pointwise_bwd(x0, enc[0], dh, enc[1], act=1)
+    return loss, {"x0": ge["dx"], "enc": (ge["dw"], ge["db"]), "blocks": gblocks,
+                  "dec": (gd["dw"], gd["db"]), "h": h, "y": y}

@@ -39,6 +39,9 @@
  * tables of exp(2 pi i r/N) indexed by the exact integer residue r = k n mod N.
  * The brute-force routines evaluate the full 4-D sums literally with their own
  * cos/sin calls, for tiny shapes.
+ *
+ * Around the blocks (Alg. 1): the encoder and decoder pointwise 1x1 layers
+ * with sigma, and the mean-squared-error loss, at the end of this file.
  */
 #include <math.h>
 #include <stdint.h>
@@ -53,8 +56,10 @@
 /* Mutation hooks for the pin tests: a test build defines ORACLE_MUTANT = k to
  * plant one known slip (1 stored-index map off by one, 2 dropped c(kt),
  * 3 wrong sign of the t exponent, 4 missing 1/N, 5 transposed W_l in the
- * forward, 6 conjugate dropped in dW, 7 GELU' without its second term) and
- * checks that some pin fails.  The oracle itself is built with 0. */
+ * forward, 6 conjugate dropped in dW, 7 GELU' without its second term,
+ * 8 bias dropped in the pointwise layer, 9 loss gradient without its factor 2,
+ * 10 pointwise sigma' taken at sigma(A) instead of A) and checks that some pin
+ * fails.  The oracle itself is built with 0. */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
 #endif
@@ -723,4 +728,107 @@ done:
   work_free(&wk);
   tables_free(&T);
   return rc;
+}
+
+/* ======================================================================== */
+/* The layers around the blocks (Alg. 1): encoder and decoder 1x1 layers,    */
+/* and the training loss                                                     */
+/* ======================================================================== */
+/*
+ * Pointwise channel layer (Alg. 1's encoder X W^e and decoder X W^d, each
+ * followed by sigma; the bias of the original FNO's 1x1 layers is optional):
+ *   A[b,o,p] = sum_i X[b,i,p] W[i,o] + bias[o]      W stored [Ci][Co]
+ *   Y        = sigma(A),  sigma = identity (act 0) or GELU (act 1)
+ * Gradient for an upstream dY:
+ *   dA = dY sigma'(A);  dX[b,i,p] = sum_o W[i,o] dA[b,o,p]
+ *   dW[i,o] = sum_{b,p} X[b,i,p] dA[b,o,p];  db[o] = sum_{b,p} dA[b,o,p]
+ * Loss (mean squared error against a target T over n values):
+ *   L = (1/n) sum (Y - T)^2;  dY = (2/n) (Y - T)
+ */
+static double pw_pre(int64_t Ci, int64_t Co, int64_t P, int dtype, const void* x, const void* w,
+                     const void* bias, int64_t b, int64_t o, int64_t p) {
+  double a = (bias && !MUT(8)) ? ld(bias, dtype, o) : 0.0;
+  for (int64_t i = 0; i < Ci; ++i) a += ld(x, dtype, (b * Ci + i) * P + p) * ld(w, dtype, i * Co + o);
+  return a;
+}
+
+int oracle_pointwise_fwd(int64_t B, int64_t Ci, int64_t Co, int64_t P, int act, int dtype,
+                         const void* x, const void* w, const void* bias, double* y) {
+  if (B < 0 || Ci < 1 || Co < 1 || P < 0 || (act != 0 && act != 1) || !w || !y) return ORC_EINVAL;
+  if (B * P > 0 && !x) return ORC_EINVAL;
+  for (int64_t b = 0; b < B; ++b)
+    for (int64_t o = 0; o < Co; ++o) {
+#pragma omp parallel for schedule(static)
+      for (int64_t p = 0; p < P; ++p) {
+        const double a = pw_pre(Ci, Co, P, dtype, x, w, bias, b, o, p);
+        y[(b * Co + o) * P + p] = act ? gelu(a) : a;
+      }
+    }
+  return ORC_OK;
+}
+
+int oracle_pointwise_bwd(int64_t B, int64_t Ci, int64_t Co, int64_t P, int act, int dtype,
+                         const void* x, const void* w, const void* bias, const void* dy,
+                         double* dx, double* dw, double* db) {
+  if (B < 0 || Ci < 1 || Co < 1 || P < 0 || (act != 0 && act != 1) || !w || !dw) return ORC_EINVAL;
+  if (B * P > 0 && (!x || !dy)) return ORC_EINVAL;
+  double* da = (double*)malloc(sizeof(double) * (size_t)(B * Co * P > 0 ? B * Co * P : 1));
+  if (!da) return ORC_ENOMEM;
+  for (int64_t b = 0; b < B; ++b)
+    for (int64_t o = 0; o < Co; ++o) {
+#pragma omp parallel for schedule(static)
+      for (int64_t p = 0; p < P; ++p) {
+        const int64_t e = (b * Co + o) * P + p;
+        double s = 1.0;
+        if (act) {
+          const double a = pw_pre(Ci, Co, P, dtype, x, w, bias, b, o, p);
+          s = gelu_grad(MUT(10) ? gelu(a) : a);
+        }
+        da[e] = ld(dy, dtype, e) * s;
+      }
+    }
+  for (int64_t i = 0; i < Ci; ++i)
+    for (int64_t o = 0; o < Co; ++o) {
+      double acc = 0.0;
+      for (int64_t b = 0; b < B; ++b) {
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+        for (int64_t p = 0; p < P; ++p)
+          acc += ld(x, dtype, (b * Ci + i) * P + p) * da[(b * Co + o) * P + p];
+      }
+      dw[i * Co + o] = acc;
+    }
+  if (db)
+    for (int64_t o = 0; o < Co; ++o) {
+      double acc = 0.0;
+      for (int64_t b = 0; b < B; ++b) {
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+        for (int64_t p = 0; p < P; ++p) acc += da[(b * Co + o) * P + p];
+      }
+      db[o] = acc;
+    }
+  if (dx)
+    for (int64_t b = 0; b < B; ++b)
+      for (int64_t i = 0; i < Ci; ++i) {
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < P; ++p) {
+          double s = 0.0;
+          for (int64_t o = 0; o < Co; ++o) s += ld(w, dtype, i * Co + o) * da[(b * Co + o) * P + p];
+          dx[(b * Ci + i) * P + p] = s;
+        }
+      }
+  free(da);
+  return ORC_OK;
+}
+
+int oracle_mse(int64_t n, int dtype, const void* y, const void* t, double* loss, double* dy) {
+  if (n < 1 || !y || !t || !loss) return ORC_EINVAL;
+  double acc = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+  for (int64_t e = 0; e < n; ++e) {
+    const double r = ld(y, dtype, e) - ld(t, dtype, e);
+    acc += r * r;
+    if (dy) dy[e] = (MUT(9) ? 1.0 : 2.0) * r / (double)n;
+  }
+  *loss = acc / (double)n;
+  return ORC_OK;
 }

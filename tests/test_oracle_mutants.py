@@ -3,14 +3,18 @@
 `oracle.mutant(k)` swaps in a build of the same C source compiled with
 ORACLE_MUTANT = k, which plants exactly one mistake: a stored-index map off by
 one, a dropped c(kt) weight, a wrong sign of the t exponent, a missing 1/N, a
-transposed bypass weight, a conjugate dropped in the weight gradient, or a
-GELU derivative missing its second term.  For every mutant at least one pin
-of tests/test_oracle_pins.py must fail; the unmutated oracle passes them all.
+transposed bypass weight, a conjugate dropped in the weight gradient, a
+GELU derivative missing its second term, a bias dropped in the pointwise
+encoder/decoder layer, a loss gradient missing its factor 2, or the pointwise
+layer's GELU derivative taken at GELU(A) instead of A.  For every mutant at
+least one pin of tests/test_oracle_pins.py or tests/test_oracle_stack_pins.py
+must fail; the unmutated oracle passes them all.
 """
 import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_stack_pins as spins
 
 PINS = {
     "rfftn corners": lambda: pins.test_spectrum_equals_numpy_rfftn_kept_corners(pins.TINY[1]),
@@ -21,6 +25,10 @@ PINS = {
     "finite differences": pins.test_block_gradient_central_finite_differences,
     "linear+gelu special case": pins.test_zero_spectral_weight_reduces_to_torch_linear_gelu,
     "gelu values": pins.test_gelu_textbook_values,
+    "pointwise vs torch": lambda: spins.test_pointwise_forward_equals_torch_linear_and_gelu(1),
+    "pointwise grad vs torch": lambda: spins.test_pointwise_gradient_equals_torch_autograd(1),
+    "mse vs torch": spins.test_mse_equals_torch_mse_loss_and_its_gradient,
+    "stack finite differences": spins.test_stack_gradient_central_finite_differences,
 }
 
 MUTANTS = {
@@ -31,6 +39,9 @@ MUTANTS = {
     5: "transposed W_l in the forward",
     6: "conjugate dropped in dW",
     7: "GELU' without its second term",
+    8: "bias dropped in the pointwise layer",
+    9: "loss gradient without its factor 2",
+    10: "pointwise GELU' taken at GELU(A)",
 }
 
 
