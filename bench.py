@@ -38,6 +38,12 @@ WORKLOADS = {
     "co2_block_128c_t32": (1, 20, 128, 128, 128, 32, 12, 12, 8, 8, (20.0, 20.0, 4.0, 8.0)),
     "ns_block_64c_t16": (2, 20, 64, 64, 64, 16, 8, 8, 8, 6, (8.0, 8.0, 8.0, 8.0)),
 }
+# The Alg. 1 stacks (encoder 1x1, FNO blocks, decoder 1x1, MSE loss), one training
+# pass per step:  name: (B, C_in, width, C_out, Nx, Ny, Nz, Nt, mx, my, mz, mt, blocks, inputs)
+STACKS = {
+    "co2_stack_128c_t32": (1, 3, 20, 1, 128, 128, 128, 32, 12, 12, 8, 8, 4, "co2"),
+    "ns_stack_64c_t32": (8, 4, 32, 4, 64, 64, 64, 32, 12, 12, 12, 8, 4, "ns"),
+}
 DEFAULT_WORKLOAD = "co2_block_128c_t32"
 METRIC = "spectral block fwd+bwd Gpoint·ch/s & roofline %, BF16/split vs FP32 @ stated err"
 UNIT = "Gpoint*ch/s"
@@ -151,8 +157,9 @@ TRAFFIC_PER_UNIT = {
     "fno_epi_fwd_f32": (0.805e9 + 0.6312e9) / 167772160,
     "fno_epi_da_f32": (1.476e9 + 0.646e9) / 167772160,
     "fno_epi_dx_f32": (0.8049e9 + 0.6129e9) / 167772160,
-    "fno_epi_fwd_mma_bf16x3": (0.800946e9 + 0.6336622e9) / 167772160,
-    "fno_epi_da_mma_bf16x3": (1.470072e9 + 0.646274e9) / 167772160,
+    "fno_epi_fwd_mma_bf16x3": (0.801082e9 + 0.633694e9) / 167772160,
+    "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
+    "fno_epi_dx_mma_bf16x3": (0.800936e9 + 0.616677e9) / 167772160,
     "fno_fwd_tz_tc_bf16x3": (0.6712366e9 + 0.1125819e9) / 167772160,
 }
 
@@ -275,8 +282,62 @@ def oracle_sample_time(wl_name, sample_channels, seed=1000):
     return dt, units, cores, f"B=1, C_in=C_out={c} on the {Nx}x{Ny}x{Nz}x{Nt} grid, modes {mx}/{my}/{mz}/{mt}"
 
 
+def stack_arrays(name, cfg, width=None, batch=None):
+    """Seeded input, target and parameters of a stack workload (NumPy, float32)."""
+    from paper_2211_12709_gb300 import inputs
+    B, C0, W, Co, Nx, Ny, Nz, Nt, mx, my, mz, mt, L, kind = STACKS[name]
+    B = batch or B
+    W = width or W
+    grid = (Nx, Ny, Nz, Nt)
+    gen = inputs.co2_stack_inputs if kind == "co2" else inputs.ns_stack_inputs
+    x0, target = gen(B, grid, inputs.SEED_INPUT + cfg)
+    enc = inputs.linear_params(C0, W, inputs.SEED_LINEAR + cfg)
+    blocks = []
+    for k in range(L):
+        w = inputs.spectral_weights(W, W, (2 * mx, 2 * my, 2 * mz, mt), inputs.SEED_SPECTRAL_W + cfg + k)
+        wl, bb = inputs.linear_params(W, W, inputs.SEED_LINEAR + cfg + 10 + k)
+        blocks.append((w, wl, bb))
+    dec = inputs.linear_params(W, Co, inputs.SEED_LINEAR + cfg + 20)
+    return x0, target, enc, blocks, dec
+
+
+def oracle_stack_time(name, width=2, seed=0):
+    """Seconds of one oracle training pass of a stack on its grid with a narrower width."""
+    import oracle
+    from oracle import Dims
+    B, C0, W, Co, Nx, Ny, Nz, Nt, mx, my, mz, mt, L, kind = STACKS[name]
+    x0, target, enc, blocks, dec = stack_arrays(name, seed, width=width, batch=1)
+    d = Dims(1, width, width, Nx, Ny, Nz, Nt, mx, my, mz, mt)
+    cores = oracle.threads()
+    t0 = time.perf_counter()
+    oracle.stack_loss_and_grads(d, x0, target, enc, blocks, dec)
+    dt = time.perf_counter() - t0
+    units = width * d.n_grid * L
+    return dt, units, cores, (f"B=1, width {width} (C_in {C0}, C_out {Co}), {L} blocks on the "
+                              f"{Nx}x{Ny}x{Nz}x{Nt} grid, modes {mx}/{my}/{mz}/{mt}")
+
+
 def run_reference(args, rank, world):
     if rank != 0:
+        return 0
+    if args.workload in STACKS:
+        dts = []
+        if args.warmup > 0:
+            oracle_stack_time(args.workload)
+        for _ in range(args.steps):
+            dt, units, cores, sample = oracle_stack_time(args.workload)
+            dts.append(dt)
+        tot = sum(dts)
+        value = units * len(dts) / tot / 1e9
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(dts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
         return 0
     wl_name = args.workload
     B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[wl_name]
@@ -302,6 +363,129 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_stack(args, rank, world, local, dev, dist):
+    """One training pass of an Alg. 1 stack per step, through StackRunner (C ABI only)."""
+    import numpy as np
+    import torch
+
+    from paper_2211_12709_gb300 import _lib
+    from paper_2211_12709_gb300.stack import StackRunner
+
+    B, C0, W, Co, Nx, Ny, Nz, Nt, mx, my, mz, mt, L, kind = STACKS[args.workload]
+    grid = (Nx, Ny, Nz, Nt)
+    Ng = Nx * Ny * Nz * Nt
+    cfg = replica_seed(rank)
+    x0_np, tg_np, enc, blocks, dec = stack_arrays(args.workload, cfg)
+    x0_h = torch.from_numpy(x0_np).pin_memory()
+    tg_h = torch.from_numpy(tg_np).pin_memory()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    params = {"enc_w": T(enc[0]), "enc_b": T(enc[1]), "dec_w": T(dec[0]), "dec_b": T(dec[1]),
+              "blocks": [tuple(T(a) for a in blk) for blk in blocks]}
+    x0 = x0_h.to(dev)
+    tg = tg_h.to(dev)
+    runner = StackRunner(B, C0, grid, params, (mx, my, mz, mt), args.precision, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        runner.step(x0, tg)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    n0 = _lib.fno_launch_count()
+    _lib.fno_profile_start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        runner.step(x0, tg)
+    e1.record(stream)
+    barrier()
+    prof = _lib.fno_profile_stop()
+    launches = _lib.fno_launch_count() - n0
+    clocks = sampler.stop()
+    ms = reduce_step_time(e0.elapsed_time(e1) / args.steps, dist, dev)
+    units = B * W * Ng * L  # point-channels through the blocks per step
+    value = whole_job_value(units, world, ms)
+    loss = float(runner.loss.item())
+
+    e2e = None
+    if not args.no_e2e:
+        grads = [runner.grads["enc_w"], runner.grads["enc_b"], runner.grads["dec_w"],
+                 runner.grads["dec_b"]] + [t for blk in runner.grads["blocks"] for t in blk]
+        outs = [runner.loss] + grads
+        outs_h = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+        h2d = (x0_h.numel() + tg_h.numel()) * 4
+        d2h = sum(t.numel() * 4 for t in outs_h)
+        k2 = max(2, min(args.steps, 5))
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(k2):
+            x0.copy_(x0_h, non_blocking=True)
+            tg.copy_(tg_h, non_blocking=True)
+            runner.step(x0, tg)
+            for hb, db_ in zip(outs_h, outs):
+                hb.copy_(db_, non_blocking=True)
+        e3.record(stream)
+        barrier()
+        ms2 = reduce_step_time(e2.elapsed_time(e3) / k2, dist, dev)
+        e2e = {"value": whole_job_value(units, world, ms2), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms2}
+
+    pk = peaks()
+    dd = {"B": B, "Ci": W, "Co": W, "Nx": Nx, "Ny": Ny, "Nz": Nz, "Nt": Nt,
+          "Jx": 2 * mx, "Jy": 2 * my, "Jz": 2 * mz, "Jt": mt}
+    tot_prof = sum(v[1] for v in prof.values()) if prof else 0.0
+    kernel_share = {}
+    for k, (n, t) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        r = roofline_of(k, t / n, dd, pk, args.precision)
+        kernel_share[k] = {"launches": n, "ms": round(t, 4),
+                           "share": round(t / tot_prof, 4) if tot_prof else None,
+                           "bound": r["bound"] if r else None, "frac": r["frac"] if r else None}
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = roofline_of(top[0], top[1][1] / top[1][0], dd, pk, args.precision) if top else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            dt, u, cores, sample = oracle_stack_time(args.workload)
+            cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32+f32", "bf16": "bf16+f32",
+                                           "bf16x3": "bf16x3+f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "B": B, "C_in": C0, "width": W, "C_out": Co,
+                       "blocks": L, "grid": list(grid), "modes": [mx, my, mz, mt],
+                       "precision": args.precision,
+                       "step": "encoder 1x1+GELU, FNO blocks, decoder 1x1+GELU, MSE loss; forward "
+                               "and backward, block inputs kept, spectra recomputed (Alg. 1)",
+                       "units": "B*width*N per block, summed over the blocks",
+                       "l2": "activations larger than L2; no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "loss": loss, "bytes_held": runner.bytes_held(),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "kernels": kernel_share,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,7 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16", "bf16x3"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(STACKS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
@@ -335,6 +519,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.workload in STACKS:
+        return run_stack(args, rank, world, local, dev, dist)
 
     B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[args.workload]
     modes = (mx, my, mz, mt)

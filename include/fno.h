@@ -154,6 +154,50 @@ int fno_profile_stop(void);
 int fno_profile_count(void);
 int fno_profile_entry(int i, const char** name, int64_t* launches, double* total_ms);
 
+/* ---- layers around the blocks (Alg. 1) --------------------------------------
+ * Alg. 1 wraps the FNO blocks in an encoder, a 1x1 convolution that lifts the
+ * input channels to the width, and a decoder, a 1x1 convolution that brings the
+ * width down to the output channels; each is followed by sigma.  The
+ * pointwise layer is that 1x1 convolution over P points per channel (P = Nx Ny
+ * Nz Nt on the 4-D grid), with an optional bias (the original FNO's 1x1 layers
+ * carry one):
+ *
+ *   y[b,o,p] = act( sum_i x[b,i,p] w[i,o] + bias[o] )    act: FNO_ACT_NONE or
+ *                                                        FNO_ACT_GELU (erf form)
+ * Layouts (C-contiguous FP32, device memory): x, dx [B][C_in][P]; y, dy
+ * [B][C_out][P]; w, dw [C_in][C_out]; bias, db [C_out].  1 <= C_in, C_out <= 64,
+ * B >= 0, P >= 0 (an empty input gives zero dw, db).  FP32 on the CUDA cores in
+ * every precision: with so few channels these layers are bound by HBM. */
+typedef struct fno_pw_dims {
+  int64_t B, C_in, C_out, P;
+} fno_pw_dims;
+
+typedef enum fno_act { FNO_ACT_NONE = 0, FNO_ACT_GELU = 1 } fno_act;
+
+/* Forward.  bias nullable (zero).  No workspace. */
+int fno_pointwise_fwd(const fno_pw_dims* dims, int act, const float* x, const float* w,
+                      const float* bias, float* y, void* stream);
+
+/* Workspace bytes of fno_pointwise_bwd for these sizes on the current device
+ * (0 on invalid arguments). */
+size_t fno_pointwise_workspace_bytes(const fno_pw_dims* dims);
+
+/* Backward for upstream gradient dy: dA = dy act'(A) (A recomputed from x);
+ * dx = w dA (nullable: the encoder's input needs none); dw = sum x dA^T and
+ * db = sum dA over batch and points (db nullable), reduced in a fixed order. */
+int fno_pointwise_bwd(const fno_pw_dims* dims, int act, const float* x, const float* w,
+                      const float* bias, const float* dy, float* dx, float* dw, float* db,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes of fno_mse_loss on the current device. */
+size_t fno_mse_workspace_bytes(int64_t n);
+
+/* Mean-squared-error training loss over n >= 1 values: *loss = (1/n) sum
+ * (y - target)^2 (one device float), dy = (2/n)(y - target) (nullable), the sum
+ * reduced in a fixed order. */
+int fno_mse_loss(int64_t n, const float* y, const float* target, float* loss, float* dy,
+                 void* ws, size_t ws_bytes, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot hand the library a workspace: for example a host program whose own

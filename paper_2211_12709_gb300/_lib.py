@@ -23,13 +23,20 @@ EXPORTS = (
     "fno_workspace_bytes", "fno_spectral_fwd", "fno_spectral_bwd", "fno_block_fwd",
     "fno_block_bwd", "fno_last_error", "fno_version", "fno_launch_count", "fno_profile_start",
     "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static", "fno_workspace_status", "fno_last_status",
+    "fno_pointwise_fwd", "fno_pointwise_workspace_bytes", "fno_pointwise_bwd",
+    "fno_mse_workspace_bytes", "fno_mse_loss",
 )
+FNO_ACT_NONE, FNO_ACT_GELU = 0, 1
 FNO_STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class fno_dims(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("B", "C_in", "C_out", "Nx", "Ny", "Nz", "Nt", "mx", "my", "mz", "mt")]
+
+
+class fno_pw_dims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("B", "C_in", "C_out", "P")]
 
 
 class FnoError(RuntimeError):
@@ -83,6 +90,17 @@ def load(build_if_needed: bool = True):
         lib.fno_profile_entry.argtypes = [ci, ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
         lib.fno_profile_entry.restype = ci
+        pp = ctypes.POINTER(fno_pw_dims)
+        lib.fno_pointwise_fwd.argtypes = [pp, ci, vp, vp, vp, vp, vp]
+        lib.fno_pointwise_fwd.restype = ci
+        lib.fno_pointwise_workspace_bytes.argtypes = [pp]
+        lib.fno_pointwise_workspace_bytes.restype = sz
+        lib.fno_pointwise_bwd.argtypes = [pp, ci, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        lib.fno_pointwise_bwd.restype = ci
+        lib.fno_mse_workspace_bytes.argtypes = [i64]
+        lib.fno_mse_workspace_bytes.restype = sz
+        lib.fno_mse_loss.argtypes = [i64, vp, vp, vp, vp, vp, sz, vp]
+        lib.fno_mse_loss.restype = ci
         _lib = lib
         return lib
 
@@ -166,3 +184,36 @@ def fno_profile_stop():
         _check(lib.fno_profile_entry(i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)))
         out[name.value.decode()] = (int(n.value), float(ms.value))
     return out
+
+
+def make_pw_dims(B, C_in, C_out, P) -> fno_pw_dims:
+    return fno_pw_dims(int(B), int(C_in), int(C_out), int(P))
+
+
+def fno_pointwise_fwd(dims, act, x, w, bias, y, stream=0):
+    _check(load().fno_pointwise_fwd(ctypes.byref(dims), int(act), x, w, bias, y, stream))
+
+
+def fno_pointwise_workspace_bytes(dims) -> int:
+    lib = load()
+    n = lib.fno_pointwise_workspace_bytes(ctypes.byref(dims))
+    if n == 0:
+        raise FnoError(int(lib.fno_last_status()), fno_last_error())
+    return int(n)
+
+
+def fno_pointwise_bwd(dims, act, x, w, bias, dy, dx, dw, db, ws, ws_bytes, stream=0):
+    _check(load().fno_pointwise_bwd(ctypes.byref(dims), int(act), x, w, bias, dy, dx, dw, db, ws,
+                                    ws_bytes, stream))
+
+
+def fno_mse_workspace_bytes(n: int) -> int:
+    lib = load()
+    r = lib.fno_mse_workspace_bytes(int(n))
+    if r == 0:
+        raise FnoError(int(lib.fno_last_status()), fno_last_error())
+    return int(r)
+
+
+def fno_mse_loss(n, y, target, loss, dy, ws, ws_bytes, stream=0):
+    _check(load().fno_mse_loss(int(n), y, target, loss, dy, ws, ws_bytes, stream))

@@ -321,6 +321,30 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   return FNO_OK;
 }
 
+// ---- layers around the blocks (Alg. 1) --------------------------------------
+static int to_pw(const fno_pw_dims* pd, int64_t* B, int* Ci, int* Co, int64_t* P) {
+  if (!pd) return fail(FNO_ERR_INVALID_ARG, "dims is NULL");
+  if (pd->B < 0) return fail(FNO_ERR_INVALID_ARG, "B = %lld < 0", (long long)pd->B);
+  if (pd->P < 0) return fail(FNO_ERR_INVALID_ARG, "P = %lld < 0", (long long)pd->P);
+  if (pd->C_in < 1 || pd->C_in > kMaxChannels || pd->C_out < 1 || pd->C_out > kMaxChannels)
+    return fail(FNO_ERR_INVALID_ARG, "C_in = %lld, C_out = %lld must lie in 1..%lld",
+                (long long)pd->C_in, (long long)pd->C_out, (long long)kMaxChannels);
+  if (pd->P > ((int64_t)1 << 40) || pd->B > ((int64_t)1 << 20))
+    return fail(FNO_ERR_INVALID_ARG, "B = %lld, P = %lld too large", (long long)pd->B,
+                (long long)pd->P);
+  *B = pd->B;
+  *Ci = (int)pd->C_in;
+  *Co = (int)pd->C_out;
+  *P = pd->P;
+  return FNO_OK;
+}
+
+static size_t pw_ws_bytes(int Ci, int Co) {
+  // per-CTA partial rows, then a db scratch for callers that pass db = NULL
+  return align256(sizeof(float) * (size_t)pointwise_max_grid(Ci, Co) * (size_t)(Ci * Co + Co)) +
+         align256(sizeof(float) * (size_t)Co);
+}
+
 }  // namespace fno
 
 using namespace fno;
@@ -486,6 +510,89 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   return FNO_OK;
 }
 
+size_t fno_pointwise_workspace_bytes(const fno_pw_dims* dims) {
+  int64_t B, P;
+  int Ci, Co;
+  if (to_pw(dims, &B, &Ci, &Co, &P)) return 0;
+  return pw_ws_bytes(Ci, Co);
+}
+
+int fno_pointwise_fwd(const fno_pw_dims* dims, int act, const float* x, const float* w,
+                      const float* bias, float* y, void* stream) {
+  int64_t B, P;
+  int Ci, Co;
+  int rc = to_pw(dims, &B, &Ci, &Co, &P);
+  if (rc) return rc;
+  if (act != FNO_ACT_NONE && act != FNO_ACT_GELU)
+    return fail(FNO_ERR_INVALID_ARG, "act = %d is not FNO_ACT_NONE or FNO_ACT_GELU", act);
+  REQ(w, 4);
+  if (bias && !aligned(bias, 4)) return fail(FNO_ERR_INVALID_ARG, "bias must be 4-byte aligned");
+  if (B * P == 0) return FNO_OK;
+  REQ(x, 4);
+  REQ(y, 4);
+  CK(launch_pointwise_fwd(x, w, bias, y, B, P, Ci, Co, act, (cudaStream_t)stream));
+  return FNO_OK;
+}
+
+int fno_pointwise_bwd(const fno_pw_dims* dims, int act, const float* x, const float* w,
+                      const float* bias, const float* dy, float* dx, float* dw, float* db,
+                      void* ws, size_t ws_bytes, void* stream) {
+  int64_t B, P;
+  int Ci, Co;
+  int rc = to_pw(dims, &B, &Ci, &Co, &P);
+  if (rc) return rc;
+  if (act != FNO_ACT_NONE && act != FNO_ACT_GELU)
+    return fail(FNO_ERR_INVALID_ARG, "act = %d is not FNO_ACT_NONE or FNO_ACT_GELU", act);
+  REQ(w, 4);
+  REQ(dw, 4);
+  if (bias && !aligned(bias, 4)) return fail(FNO_ERR_INVALID_ARG, "bias must be 4-byte aligned");
+  if (db && !aligned(db, 4)) return fail(FNO_ERR_INVALID_ARG, "db must be 4-byte aligned");
+  if (dx && !aligned(dx, 4)) return fail(FNO_ERR_INVALID_ARG, "dx must be 4-byte aligned");
+  const size_t need = pw_ws_bytes(Ci, Co);
+  if (ws_bytes < need)
+    return fail(FNO_ERR_WORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, need);
+  if (!ws) return fail(FNO_ERR_WORKSPACE, "workspace is NULL");
+  if (!aligned(ws, 256)) return fail(FNO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* part = static_cast<float*>(ws);
+  float* dbs = db ? db : reinterpret_cast<float*>(static_cast<char*>(ws) + need - align256(sizeof(float) * (size_t)Co));
+  if (B * P == 0) {
+    CK(launch_fill_zero(dw, (int64_t)Ci * Co, s));
+    if (db) CK(launch_fill_zero(db, Co, s));
+    return FNO_OK;
+  }
+  REQ(x, 4);
+  REQ(dy, 4);
+  int rows = 0;
+  CK(launch_pointwise_bwd(x, w, bias, dy, dx, part, B, P, Ci, Co, act, &rows, s));
+  CK(launch_reduce_partials(part, rows, Ci, Co, dw, dbs, s));
+  return FNO_OK;
+}
+
+size_t fno_mse_workspace_bytes(int64_t n) {
+  if (n < 1) {
+    fail(FNO_ERR_INVALID_ARG, "n = %lld must be >= 1", (long long)n);
+    return 0;
+  }
+  return align256(sizeof(float) * (size_t)mse_max_grid());
+}
+
+int fno_mse_loss(int64_t n, const float* y, const float* target, float* loss, float* dy,
+                 void* ws, size_t ws_bytes, void* stream) {
+  if (n < 1) return fail(FNO_ERR_INVALID_ARG, "n = %lld must be >= 1", (long long)n);
+  REQ(y, 4);
+  REQ(target, 4);
+  REQ(loss, 4);
+  if (dy && !aligned(dy, 4)) return fail(FNO_ERR_INVALID_ARG, "dy must be 4-byte aligned");
+  const size_t need = align256(sizeof(float) * (size_t)mse_max_grid());
+  if (ws_bytes < need)
+    return fail(FNO_ERR_WORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, need);
+  if (!ws) return fail(FNO_ERR_WORKSPACE, "workspace is NULL");
+  if (!aligned(ws, 256)) return fail(FNO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  CK(launch_mse(y, target, dy, n, loss, static_cast<float*>(ws), (cudaStream_t)stream));
+  return FNO_OK;
+}
+
 int fno_workspace_status(const void* ws, void* stream) {
   if (!ws) return fail(FNO_ERR_INVALID_ARG, "ws is NULL");
   int h = 0;
@@ -503,7 +610,7 @@ const char* fno_last_error(void) { return g_err.c_str(); }
 
 int fno_last_status(void) { return g_status; }
 
-int fno_version(void) { return 100; }
+int fno_version(void) { return 101; }
 
 int64_t fno_launch_count(void) { return g_launches.load(); }
 

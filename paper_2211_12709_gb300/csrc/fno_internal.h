@@ -107,6 +107,22 @@ cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const D
                              const float2* ft, const float2* fz, bool split, bool tf32, int* err,
                              cudaStream_t s);
 
+// ---- layers around the blocks (fno_pointwise.cu) ---------------------------
+// y[b,o,p] = act(sum_i x[b,i,p] w[i,o] + bias[o]) (bias nullable, act 0/1 = none/GELU).
+cudaError_t launch_pointwise_fwd(const float* x, const float* w, const float* bias, float* y,
+                                 int64_t B, int64_t P, int Ci, int Co, int act, cudaStream_t s);
+// dA = dy act'(A); dx = W dA (nullable); writes rows_out rows of per-CTA partial
+// sums [row][Ci*Co + Co] of (dw, db) into part, for launch_reduce_partials.
+cudaError_t launch_pointwise_bwd(const float* x, const float* w, const float* bias,
+                                 const float* dy, float* dx, float* part, int64_t B, int64_t P,
+                                 int Ci, int Co, int act, int* rows_out, cudaStream_t s);
+size_t pointwise_smem_bytes(int Ci, int Co);
+int pointwise_max_grid(int Ci, int Co);  // the most rows launch_pointwise_bwd writes
+// loss = mean((y - t)^2) into *loss, dy = 2 (y - t) / n (nullable); part: mse_max_grid() floats
+int mse_max_grid();
+cudaError_t launch_mse(const float* y, const float* t, float* dy, int64_t n, float* loss,
+                       float* part, cudaStream_t s);
+
 #ifdef __CUDACC__
 // Launch with the profiling hooks; returns the launch error from the caller.
 #define FNO_LAUNCH(name, kern, grid, block, smem, stream, ...)   \
@@ -123,6 +139,43 @@ __device__ __forceinline__ float gelu_f(float a) {
 __device__ __forceinline__ float gelu_grad_f(float a) {
   return 0.5f * (1.0f + erff(a * 0.70710678118654752440f)) +
          a * expf(-0.5f * a * a) * 0.39894228040143267794f;
+}
+
+// Phi2(a) = 1 + erf(a / sqrt 2) and exp(-a^2 / 2), with erf from Abramowitz
+// and Stegun 7.1.26: erf(u) = 1 - (a1 t + ... + a5 t^5) exp(-u^2),
+// t = 1 / (1 + p u), u >= 0, |error| < 1.5e-7.  For a < 0 the complement is
+// taken directly (no cancellation).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void phi2_as(float a, float& phi2, float& e) {
+  const float u = fabsf(a) * 0.70710678118654752f;
+  const float t = rcp_approx(fmaf(0.3275911f, u, 1.0f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  q *= t;
+  e = ex2_approx(-u * u * 1.4426950408889634f);
+  const float c = q * e;  // 1 - erf(u)
+  phi2 = (a >= 0.f) ? 2.0f - c : c;
+}
+__device__ __forceinline__ float gelu_as(float a) {
+  float phi2, e;
+  phi2_as(a, phi2, e);
+  return 0.5f * a * phi2;
+}
+__device__ __forceinline__ float gelu_grad_as(float a) {
+  float phi2, e;
+  phi2_as(a, phi2, e);
+  return fmaf(a * e, 0.39894228040143268f, 0.5f * phi2);
 }
 #endif
 

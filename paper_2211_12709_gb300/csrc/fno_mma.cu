@@ -145,42 +145,7 @@ __device__ __forceinline__ void split3(float a, float b, uint32_t& h, uint32_t& 
   l = *reinterpret_cast<const uint32_t*>(&lv);
 }
 
-// Phi2(a) = 1 + erf(a / sqrt 2) and exp(-a^2 / 2), with erf from Abramowitz
-// and Stegun 7.1.26: erf(u) = 1 - (a1 t + ... + a5 t^5) exp(-u^2),
-// t = 1 / (1 + p u), u >= 0, |error| < 1.5e-7.  For a < 0 the complement is
-// taken directly (no cancellation).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ void phi2_as(float a, float& phi2, float& e) {
-  const float u = fabsf(a) * 0.70710678118654752f;
-  const float t = rcp_approx(fmaf(0.3275911f, u, 1.0f));
-  float q = fmaf(1.061405429f, t, -1.453152027f);
-  q = fmaf(q, t, 1.421413741f);
-  q = fmaf(q, t, -0.284496736f);
-  q = fmaf(q, t, 0.254829592f);
-  q *= t;
-  e = ex2_approx(-u * u * 1.4426950408889634f);
-  const float c = q * e;  // 1 - erf(u)
-  phi2 = (a >= 0.f) ? 2.0f - c : c;
-}
-__device__ __forceinline__ float gelu_as(float a) {
-  float phi2, e;
-  phi2_as(a, phi2, e);
-  return 0.5f * a * phi2;
-}
-__device__ __forceinline__ float gelu_grad_as(float a) {
-  float phi2, e;
-  phi2_as(a, phi2, e);
-  return fmaf(a * e, 0.39894228040143268f, 0.5f * phi2);
-}
+// GELU and GELU' (gelu_as, gelu_grad_as) come from fno_internal.h.
 
 }  // namespace
 

@@ -111,3 +111,65 @@ def co2_static_fields(Nx: int, Ny: int, Nz: int, seed: int):
     well[wx, wy, :] = 1.0
     logk_std = (logk - logk.mean()) / logk.std()
     return logk_std.astype(np.float32), phi.astype(np.float32), well.astype(np.float32)
+
+
+def co2_stack_inputs(B: int, grid, seed: int):
+    """Input and target of the CO2 stack: x0 [B][3][Nx][Ny][Nz][Nt], target [B][1][...].
+
+    x0 holds the three static fields of ``co2_static_fields`` repeated along t
+    (the paper repeats its 3-D inputs along time); the target saturation is a
+    smooth field in [0, 1], the logistic function of a GRF with correlation
+    lengths 20 x 20 x 4 cells and 8 steps.
+    """
+    Nx, Ny, Nz, Nt = (int(v) for v in grid)
+    x0 = np.empty((B, 3, Nx, Ny, Nz, Nt), dtype=np.float32)
+    for b in range(B):
+        for c, f in enumerate(co2_static_fields(Nx, Ny, Nz, seed + 17 * b)):
+            x0[b, c] = f[..., None]
+    z = grf((B, 1), (Nx, Ny, Nz, Nt), (20.0, 20.0, 4.0, 8.0), seed + 1)
+    target = (1.0 / (1.0 + np.exp(-z))).astype(np.float32)
+    return x0, target
+
+
+def ns_stack_inputs(B: int, grid, seed: int, kmax: float = 16.0):
+    """Input and target of the Navier-Stokes stack: x0, target [B][4][Nx][Ny][Nz][Nt].
+
+    Channels (u, v, w, |omega|) of a divergence-free random Fourier velocity
+    field: complex Gaussian amplitudes projected perpendicular to k, with
+    |u_hat(k)|^2 proportional to k^(-5/3) / (4 pi k^2) for 1 <= |k| <= kmax and
+    zero beyond, each mode rotating in time as exp(2 pi i f_k t / Nt) with a
+    seeded f_k in {0..3}; the vorticity is the spectral curl.  The velocity is
+    scaled to unit root-mean-square (one factor for all three components, so
+    div u = 0 holds) and |omega| to zero mean and unit standard deviation.  The
+    target is the same field one time step later (the next state).
+    """
+    Nx, Ny, Nz, Nt = (int(v) for v in grid)
+    g = _rng(seed)
+    ks = [np.fft.fftfreq(n, 1.0 / n) for n in (Nx, Ny, Nz)]
+    K = np.stack(np.meshgrid(*ks, indexing="ij"))          # [3][Nx][Ny][Nz]
+    kmag = np.sqrt((K ** 2).sum(axis=0))
+    keep = (kmag >= 1.0) & (kmag <= kmax)
+    amp = np.zeros_like(kmag)
+    amp[keep] = np.sqrt(kmag[keep] ** (-5.0 / 3.0) / (4.0 * math.pi * kmag[keep] ** 2))
+    khat = K / np.where(kmag > 0, kmag, 1.0)
+    x0 = np.empty((B, 4, Nx, Ny, Nz, Nt), dtype=np.float32)
+    for b in range(B):
+        a = g.standard_normal((3, Nx, Ny, Nz)) + 1j * g.standard_normal((3, Nx, Ny, Nz))
+        a -= khat * (a * khat).sum(axis=0)                  # k . u_hat = 0
+        uh = a * amp
+        f = g.integers(0, 4, size=(Nx, Ny, Nz))
+        for t in range(Nt):
+            uht = uh * np.exp(2j * math.pi * f * t / Nt)
+            u = _sfft.ifftn(uht, axes=(1, 2, 3), workers=_WORKERS).real
+            wh = 1j * np.cross(K, uht, axis=0)               # curl in Fourier space
+            w = _sfft.ifftn(wh, axes=(1, 2, 3), workers=_WORKERS).real
+            x0[b, 0:3, ..., t] = u
+            x0[b, 3, ..., t] = np.sqrt((w ** 2).sum(axis=0))
+    # one scale for the three velocity components (keeps div u = 0), one for |omega|
+    vel = x0[:, 0:3]
+    vel /= max(float(np.sqrt((vel.astype(np.float64) ** 2).mean())), 1e-30)
+    vort = x0[:, 3]
+    vort -= vort.mean(dtype=np.float64)
+    vort /= max(float(vort.std(dtype=np.float64)), 1e-30)
+    target = np.roll(x0, -1, axis=-1)
+    return x0, target

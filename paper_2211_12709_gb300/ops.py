@@ -207,3 +207,113 @@ class FNOBlock4d(torch.nn.Module):
 
     def forward(self, x):
         return FNOBlock4dFn.apply(x, self.weight, self.w_lin, self.bias, self.modes, self.precision)
+
+
+# ---------------------------------------------------------------------------
+# Layers around the blocks (Alg. 1): pointwise encoder/decoder, MSE loss
+# ---------------------------------------------------------------------------
+ACT = {"none": _lib.FNO_ACT_NONE, "gelu": _lib.FNO_ACT_GELU}
+
+
+def _act_code(act) -> int:
+    if isinstance(act, int):
+        return act
+    try:
+        return ACT[act]
+    except KeyError:
+        raise ValueError(f"unknown activation {act!r}; one of {sorted(ACT)}") from None
+
+
+def _pw_dims(x: torch.Tensor, C_out: int):
+    if x.dim() < 2:
+        raise ValueError(f"x must be [B, C, ...], got shape {tuple(x.shape)}")
+    B, Ci = int(x.shape[0]), int(x.shape[1])
+    P = 1
+    for v in x.shape[2:]:
+        P *= int(v)
+    return _lib.make_pw_dims(B, Ci, C_out, P)
+
+
+def pointwise_fwd(x, w, bias=None, act="gelu"):
+    """y[b,o,...] = act(sum_i x[b,i,...] w[i,o] + bias[o]): the 1x1 layers of Alg. 1."""
+    x = _req(x, "x")
+    Ci, Co = int(x.shape[1]), int(w.shape[1])
+    w = _req(w, "w", (Ci, Co))
+    bias = None if bias is None else _req(bias, "bias", (Co,))
+    d = _pw_dims(x, Co)
+    y = torch.empty((x.shape[0], Co) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
+    _lib.fno_pointwise_fwd(d, _act_code(act), x.data_ptr(), w.data_ptr(),
+                           None if bias is None else bias.data_ptr(), y.data_ptr(),
+                           _stream_handle(x.device))
+    return y
+
+
+def pointwise_bwd(x, w, bias, dy, act="gelu", need_dx=True):
+    """(dx or None, dw, db or None) of ``pointwise_fwd`` for upstream dy."""
+    x = _req(x, "x")
+    Ci, Co = int(x.shape[1]), int(w.shape[1])
+    w = _req(w, "w", (Ci, Co))
+    bias = None if bias is None else _req(bias, "bias", (Co,))
+    dy = _req(dy, "dy", (x.shape[0], Co) + tuple(x.shape[2:]))
+    d = _pw_dims(x, Co)
+    dx = torch.empty_like(x) if need_dx else None
+    dw = torch.empty_like(w)
+    db = None if bias is None else torch.empty_like(bias)
+    n = _lib.fno_pointwise_workspace_bytes(d)
+    ws = torch.empty(n, dtype=torch.uint8, device=x.device)
+    _lib.fno_pointwise_bwd(d, _act_code(act), x.data_ptr(), w.data_ptr(),
+                           None if bias is None else bias.data_ptr(), dy.data_ptr(),
+                           None if dx is None else dx.data_ptr(), dw.data_ptr(),
+                           None if db is None else db.data_ptr(), ws.data_ptr(), n,
+                           _stream_handle(x.device))
+    return dx, dw, db
+
+
+def mse_loss(y, target, need_grad=True):
+    """(loss [1] device tensor, dL/dy or None) of mean((y - target)^2)."""
+    y = _req(y, "y")
+    target = _req(target, "target", tuple(y.shape))
+    n = y.numel()
+    loss = torch.empty(1, dtype=torch.float32, device=y.device)
+    dy = torch.empty_like(y) if need_grad else None
+    nb = _lib.fno_mse_workspace_bytes(n)
+    ws = torch.empty(nb, dtype=torch.uint8, device=y.device)
+    _lib.fno_mse_loss(n, y.data_ptr(), target.data_ptr(), loss.data_ptr(),
+                      None if dy is None else dy.data_ptr(), ws.data_ptr(), nb,
+                      _stream_handle(y.device))
+    return loss, dy
+
+
+class PointwiseFn(torch.autograd.Function):
+    """The encoder / decoder 1x1 layer with sigma.  Only its input is kept."""
+
+    @staticmethod
+    def forward(ctx, x, w, bias, act="gelu"):
+        ctx.act = act
+        ctx.has_bias = bias is not None
+        ctx.save_for_backward(x, w, bias)
+        return pointwise_fwd(x, w, bias, act)
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, w, bias = ctx.saved_tensors
+        dx, dw, db = pointwise_bwd(x, w, bias if ctx.has_bias else None, dy.contiguous(),
+                                   ctx.act, need_dx=ctx.needs_input_grad[0])
+        return dx, dw, db, None
+
+
+class MSELossFn(torch.autograd.Function):
+    """mean((y - target)^2); the gradient with respect to y is formed in the forward."""
+
+    @staticmethod
+    def forward(ctx, y, target):
+        loss, dy = mse_loss(y, target, need_grad=ctx.needs_input_grad[0])
+        ctx.save_for_backward(dy if dy is not None else loss)
+        return loss.reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        (dy,) = ctx.saved_tensors
+        if not ctx.needs_input_grad[0]:
+            return None, None
+        return dy * g, None

@@ -99,3 +99,42 @@ def test_too_many_channels_is_unsupported_not_a_crash():
     d.C_in = 65
     assert raw_ws(d, 0, _lib.FNO_OP_BLOCK_FWD) == 0
     assert "<=" in _lib.fno_last_error()
+
+
+def test_pointwise_and_loss_arguments_are_checked_on_the_host():
+    lib = _lib.load()
+    d = _lib.make_pw_dims(1, 3, 20, 4096)
+    need = _lib.fno_pointwise_workspace_bytes(d)
+    assert need > 0 and need % 256 == 0
+    # channel counts outside 1..64
+    for ci, co in ((0, 4), (4, 0), (65, 4), (4, 65)):
+        bad = _lib.make_pw_dims(1, ci, co, 16)
+        assert lib.fno_pointwise_workspace_bytes(ctypes.byref(bad)) == 0
+        assert lib.fno_pointwise_fwd(ctypes.byref(bad), 1, 256, 256, None, 256, None) == -1
+    # negative sizes
+    assert lib.fno_pointwise_fwd(ctypes.byref(_lib.make_pw_dims(-1, 3, 4, 16)), 1, 256, 256, None,
+                                 256, None) == -1
+    assert lib.fno_pointwise_fwd(ctypes.byref(_lib.make_pw_dims(1, 3, 4, -16)), 1, 256, 256,
+                                 None, 256, None) == -1
+    # unknown activation, null weight, misaligned x
+    assert lib.fno_pointwise_fwd(ctypes.byref(d), 2, 256, 256, None, 256, None) == -1
+    assert lib.fno_pointwise_fwd(ctypes.byref(d), 1, 256, None, None, 256, None) == -1
+    assert "w is NULL" in _lib.fno_last_error()
+    assert lib.fno_pointwise_fwd(ctypes.byref(d), 1, 258, 256, None, 256, None) == -1
+    # an empty input needs no launch and succeeds without a GPU
+    assert lib.fno_pointwise_fwd(ctypes.byref(_lib.make_pw_dims(0, 3, 4, 16)), 1, None, 256,
+                                 None, None, None) == 0
+    # backward: workspace too small or misaligned, null dw
+    assert lib.fno_pointwise_bwd(ctypes.byref(d), 1, 256, 256, None, 256, None, 256, None, 256,
+                                 need - 256, None) == -3
+    assert lib.fno_pointwise_bwd(ctypes.byref(d), 1, 256, 256, None, 256, None, 256, None, 512 + 4,
+                                 need, None) == -3
+    assert lib.fno_pointwise_bwd(ctypes.byref(d), 1, 256, 256, None, 256, None, None, None, 256,
+                                 need, None) == -1
+    # loss: n >= 1, required pointers, workspace size
+    assert lib.fno_mse_workspace_bytes(0) == 0
+    nm = _lib.fno_mse_workspace_bytes(1000)
+    assert lib.fno_mse_loss(0, 256, 256, 256, None, 256, nm, None) == -1
+    assert lib.fno_mse_loss(1000, None, 256, 256, None, 256, nm, None) == -1
+    assert lib.fno_mse_loss(1000, 256, 256, None, None, 256, nm, None) == -1
+    assert lib.fno_mse_loss(1000, 256, 256, 256, None, 256, nm - 256, None) == -3
