@@ -43,6 +43,8 @@ WORKLOADS = {
 STACKS = {
     "co2_stack_128c_t32": (1, 3, 20, 1, 128, 128, 128, 32, 12, 12, 8, 8, 4, "co2"),
     "ns_stack_64c_t32": (8, 4, 32, 4, 64, 64, 64, 32, 12, 12, 12, 8, 4, "ns"),
+    # small case of the CO2 stack for ncu captures (a few GB on the device)
+    "co2_stack_64c_t16": (1, 3, 20, 1, 64, 64, 64, 16, 8, 8, 8, 6, 4, "co2"),
 }
 DEFAULT_WORKLOAD = "co2_block_128c_t32"
 METRIC = "spectral block fwd+bwd Gpoint·ch/s & roofline %, BF16/split vs FP32 @ stated err"
@@ -146,6 +148,12 @@ def algorithmic(name, d):
         return 3 * grid + t1, f_inv + 2 * f_lin
     if name.startswith("fno_epi_dx"):
         return 2 * grid + t1, f_inv + f_lin
+    Mk = Jx * Jy * Jz * Jt
+    nchunk = (B + 7) // 8  # batch chunks of the mixing kernels (W crosses HBM once per chunk)
+    if name.startswith("fno_mix_adjoint"):
+        return 8 * Mk * (2 * nchunk * Ci * Co + B * (2 * Ci + Co)), 16 * B * Ci * Co * Mk
+    if name.startswith("fno_mix"):
+        return 8 * Mk * (nchunk * Ci * Co + B * (Ci + Co)), 8 * B * Ci * Co * Mk
     return None, None
 
 

@@ -285,107 +285,187 @@ cudaError_t launch_line_f32(const float2* in, float2* out, int64_t outer, int ni
 }
 
 // ---------------------------------------------------------------------------
-// Spectral convolution and its adjoint (FP32).  One thread per mode j; the
-// batch is held in registers in chunks of BC.
+// Spectral convolution and its adjoint (FP32 complex multiply-adds).
+//   forward  yh[b][o][j]  = sum_i xh[b][i][j] w[i][o][j]
+//   adjoint  gxh[b][i][j] = sum_o conj(w[i][o][j]) g[b][o][j]
+//            dw[i][o][j]  = sum_b conj(xh[b][i][j]) g[b][o][j]
+// A CTA owns a tile of kMixJ consecutive modes.  It stages the tile's spectra
+// for a chunk of BC batch entries in shared memory (rows of kMixJ complex
+// values: 128-byte coalesced loads), then each thread keeps one mode j of the
+// tile (lane % kMixJ) and walks the output channels of its group (tid / kMixJ,
+// stride kMixG), reading the weights straight from HBM in coalesced 128-byte
+// rows.  W, dW and the outputs cross HBM once per batch chunk (once when
+// B <= BC), and every sum runs in a fixed order.
 // ---------------------------------------------------------------------------
-template <int BC>
-__global__ void __launch_bounds__(128)
-    k_mix_f32(const float2* __restrict__ xh, const float2* __restrict__ w, float2* __restrict__ yh,
-              int B, int Ci, int Co, long long Mk) {
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int o = blockIdx.y;
-  if (j >= Mk) return;
-  for (int b0 = 0; b0 < B; b0 += BC) {
-    float2 acc[BC];
-#pragma unroll
-    for (int q = 0; q < BC; ++q) acc[q] = make_float2(0.f, 0.f);
-    for (int i = 0; i < Ci; ++i) {
-      const float2 wv = w[((long long)i * Co + o) * Mk + j];
-#pragma unroll
-      for (int q = 0; q < BC; ++q) {
-        if (b0 + q < B) {
-          const float2 xv = xh[((long long)(b0 + q) * Ci + i) * Mk + j];
-          acc[q].x = fmaf(xv.x, wv.x, acc[q].x);
-          acc[q].x = fmaf(-xv.y, wv.y, acc[q].x);
-          acc[q].y = fmaf(xv.x, wv.y, acc[q].y);
-          acc[q].y = fmaf(xv.y, wv.x, acc[q].y);
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < BC; ++q)
-      if (b0 + q < B) yh[((long long)(b0 + q) * Co + o) * Mk + j] = acc[q];
+constexpr int kMixJ = 16;                   // modes per tile
+constexpr int kMixThreads = 256;
+constexpr int kMixG = kMixThreads / kMixJ;  // channel groups per tile
+
+__device__ __forceinline__ void cmac(float2& acc, const float2 a, const float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) b
+__device__ __forceinline__ void cmac_conj(float2& acc, const float2 a, const float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// stage src[b0 + q][c][j0 .. j0 + kMixJ) for q < nb, c < C into dst[q][c][kMixJ]
+__device__ __forceinline__ void mix_stage(float2* dst, const float2* __restrict__ src, int b0,
+                                          int nb, int BC, int C, long long Mk, long long j0) {
+  for (int e = threadIdx.x; e < BC * C * kMixJ; e += kMixThreads) {
+    const int jl = e % kMixJ, c = (e / kMixJ) % C, q = e / (kMixJ * C);
+    const long long j = j0 + jl;
+    dst[e] = (q < nb && j < Mk) ? src[((long long)(b0 + q) * C + c) * Mk + j]
+                                : make_float2(0.f, 0.f);
   }
 }
 
 template <int BC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kMixThreads)
+    k_mix_f32(const float2* __restrict__ xh, const float2* __restrict__ w, float2* __restrict__ yh,
+              int B, int Ci, int Co, long long Mk) {
+  extern __shared__ float2 mix_sm[];
+  float2* xs = mix_sm;  // [BC][Ci][kMixJ]
+  const int jl = threadIdx.x % kMixJ, grp = threadIdx.x / kMixJ;
+  const long long j0 = (long long)blockIdx.x * kMixJ, j = j0 + jl;
+  const bool inj = j < Mk;
+  for (int b0 = 0; b0 < B; b0 += BC) {
+    const int nb = min(BC, B - b0);
+    __syncthreads();
+    mix_stage(xs, xh, b0, nb, BC, Ci, Mk, j0);
+    __syncthreads();
+    if (!inj) continue;
+    for (int o = grp; o < Co; o += kMixG) {
+      float2 acc[BC];
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[q] = make_float2(0.f, 0.f);
+      const float2* wp = w + (long long)o * Mk + j;
+#pragma unroll 4
+      for (int i = 0; i < Ci; ++i) {
+        const float2 wv = __ldg(wp + (long long)i * Co * Mk);
+#pragma unroll
+        for (int q = 0; q < BC; ++q) cmac(acc[q], xs[(q * Ci + i) * kMixJ + jl], wv);
+      }
+#pragma unroll
+      for (int q = 0; q < BC; ++q)
+        if (q < nb) yh[((long long)(b0 + q) * Co + o) * Mk + j] = acc[q];
+    }
+  }
+}
+
+template <int BC>
+__global__ void __launch_bounds__(kMixThreads)
     k_mix_adj_f32(const float2* __restrict__ xh, const float2* __restrict__ w,
                   const float2* __restrict__ g, float2* __restrict__ dw, float2* __restrict__ gxh,
                   int B, int Ci, int Co, long long Mk) {
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (j >= Mk) return;
+  extern __shared__ float2 mix_sm[];
+  float2* xs = mix_sm;                   // [BC][Ci][kMixJ]
+  float2* gs = mix_sm + BC * Ci * kMixJ; // [BC][Co][kMixJ]
+  const int jl = threadIdx.x % kMixJ, grp = threadIdx.x / kMixJ;
+  const long long j0 = (long long)blockIdx.x * kMixJ, j = j0 + jl;
+  const bool inj = j < Mk;
   for (int b0 = 0; b0 < B; b0 += BC) {
-    float2 xv[BC], ga[BC];
-#pragma unroll
-    for (int q = 0; q < BC; ++q) {
-      xv[q] = (b0 + q < B) ? xh[((long long)(b0 + q) * Ci + i) * Mk + j] : make_float2(0.f, 0.f);
-      ga[q] = make_float2(0.f, 0.f);
-    }
-    for (int o = 0; o < Co; ++o) {
-      const long long widx = ((long long)i * Co + o) * Mk + j;
-      const float2 wv = w[widx];
-      float2 da = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < BC; ++q) {
-        if (b0 + q < B) {
-          const float2 gv = g[((long long)(b0 + q) * Co + o) * Mk + j];
-          // ga += conj(w) g
-          ga[q].x = fmaf(wv.x, gv.x, ga[q].x);
-          ga[q].x = fmaf(wv.y, gv.y, ga[q].x);
-          ga[q].y = fmaf(wv.x, gv.y, ga[q].y);
-          ga[q].y = fmaf(-wv.y, gv.x, ga[q].y);
-          // da += conj(xh) g
-          da.x = fmaf(xv[q].x, gv.x, da.x);
-          da.x = fmaf(xv[q].y, gv.y, da.x);
-          da.y = fmaf(xv[q].x, gv.y, da.y);
-          da.y = fmaf(-xv[q].y, gv.x, da.y);
-        }
-      }
-      if (dw) {
-        if (b0 == 0) {
-          dw[widx] = da;
-        } else {
-          float2 p = dw[widx];
-          dw[widx] = make_float2(p.x + da.x, p.y + da.y);
-        }
-      }
-    }
+    const int nb = min(BC, B - b0);
+    __syncthreads();
+    if (dw) mix_stage(xs, xh, b0, nb, BC, Ci, Mk, j0);
+    mix_stage(gs, g, b0, nb, BC, Co, Mk, j0);
+    __syncthreads();
+    if (!inj) continue;
     if (gxh) {
+      for (int i = grp; i < Ci; i += kMixG) {
+        float2 ga[BC];
 #pragma unroll
-      for (int q = 0; q < BC; ++q)
-        if (b0 + q < B) gxh[((long long)(b0 + q) * Ci + i) * Mk + j] = ga[q];
+        for (int q = 0; q < BC; ++q) ga[q] = make_float2(0.f, 0.f);
+        const float2* wp = w + (long long)i * Co * Mk + j;
+#pragma unroll 8
+        for (int o = 0; o < Co; ++o) {
+          const float2 wv = __ldg(wp + (long long)o * Mk);
+#pragma unroll
+          for (int q = 0; q < BC; ++q) cmac_conj(ga[q], wv, gs[(q * Co + o) * kMixJ + jl]);
+        }
+#pragma unroll
+        for (int q = 0; q < BC; ++q)
+          if (q < nb) gxh[((long long)(b0 + q) * Ci + i) * Mk + j] = ga[q];
+      }
+    }
+    if (dw) {
+      for (int i = 0; i < Ci; ++i) {
+        float2 xv[BC];
+#pragma unroll
+        for (int q = 0; q < BC; ++q) xv[q] = xs[(q * Ci + i) * kMixJ + jl];
+        for (int o = grp; o < Co; o += kMixG) {
+          float2 da = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < BC; ++q) cmac_conj(da, xv[q], gs[(q * Co + o) * kMixJ + jl]);
+          float2* dp = dw + ((long long)i * Co + o) * Mk + j;
+          if (b0 == 0) {
+            *dp = da;
+          } else {
+            const float2 p = *dp;
+            *dp = make_float2(p.x + da.x, p.y + da.y);
+          }
+        }
+      }
     }
   }
+}
+
+static int mix_bc(int64_t B) { return B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8; }
+
+template <int BC>
+static cudaError_t launch_mix_bc(const Dims& d, const float2* xh, const float2* w, float2* yh,
+                                 cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t)BC * (size_t)d.Ci * kMixJ;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_mix_f32<BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned grid = (unsigned)((d.Mk + kMixJ - 1) / kMixJ);
+  FNO_LAUNCH("fno_mix_f32", k_mix_f32<BC>, grid, kMixThreads, smem, s, xh, w, yh, (int)d.B,
+             (int)d.Ci, (int)d.Co, (long long)d.Mk);
+  return cudaSuccess;
+}
+
+template <int BC>
+static cudaError_t launch_mix_adj_bc(const Dims& d, const float2* xh, const float2* w,
+                                     const float2* g, float2* dw, float2* gxh, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t)BC * (size_t)(d.Ci + d.Co) * kMixJ;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_mix_adj_f32<BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned grid = (unsigned)((d.Mk + kMixJ - 1) / kMixJ);
+  FNO_LAUNCH("fno_mix_adjoint_f32", k_mix_adj_f32<BC>, grid, kMixThreads, smem, s, xh, w, g, dw,
+             gxh, (int)d.B, (int)d.Ci, (int)d.Co, (long long)d.Mk);
+  return cudaSuccess;
 }
 
 cudaError_t launch_mix_f32(const Dims& d, const float2* xh, const float2* w, float2* yh,
                            cudaStream_t s) {
   if (d.B <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((d.Mk + 127) / 128), (unsigned)d.Co);
-  FNO_LAUNCH("fno_mix_f32", k_mix_f32<4>, grid, 128, 0, s, xh, w, yh, (int)d.B, (int)d.Ci,
-             (int)d.Co, (long long)d.Mk);
-  return cudaSuccess;
+  switch (mix_bc(d.B)) {
+    case 1: return launch_mix_bc<1>(d, xh, w, yh, s);
+    case 2: return launch_mix_bc<2>(d, xh, w, yh, s);
+    case 4: return launch_mix_bc<4>(d, xh, w, yh, s);
+    default: return launch_mix_bc<8>(d, xh, w, yh, s);
+  }
 }
 
 cudaError_t launch_mix_adjoint_f32(const Dims& d, const float2* xh, const float2* w,
                                    const float2* g, float2* dw, float2* gxh, cudaStream_t s) {
   if (d.B <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((d.Mk + 127) / 128), (unsigned)d.Ci);
-  FNO_LAUNCH("fno_mix_adjoint_f32", k_mix_adj_f32<4>, grid, 128, 0, s, xh, w, g, dw, gxh,
-             (int)d.B, (int)d.Ci, (int)d.Co, (long long)d.Mk);
-  return cudaSuccess;
+  switch (mix_bc(d.B)) {
+    case 1: return launch_mix_adj_bc<1>(d, xh, w, g, dw, gxh, s);
+    case 2: return launch_mix_adj_bc<2>(d, xh, w, g, dw, gxh, s);
+    case 4: return launch_mix_adj_bc<4>(d, xh, w, g, dw, gxh, s);
+    default: return launch_mix_adj_bc<8>(d, xh, w, g, dw, gxh, s);
+  }
 }
 
 // ---------------------------------------------------------------------------

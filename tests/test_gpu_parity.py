@@ -73,6 +73,7 @@ SMALL = [
     (Dims(2, 3, 3, 8, 6, 10, 7, 4, 3, 5, 3), "2m = N on every spatial axis, odd Nt"),
     (Dims(1, 2, 4, 5, 7, 3, 12, 1, 2, 1, 7), "tiny odd grid, mt = Nt/2+1 with Nyquist"),
     (Dims(2, 17, 9, 20, 8, 40, 8, 5, 3, 7, 2), "tails: 17 channels, Nz=40"),
+    (Dims(10, 3, 2, 8, 6, 8, 4, 2, 2, 2, 2), "batch of 10: two batch chunks in the mixing"),
 ]
 
 
