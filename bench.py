@@ -168,7 +168,7 @@ TRAFFIC_PER_UNIT = {
     "fno_epi_fwd_mma_bf16x3": (0.801082e9 + 0.633694e9) / 167772160,
     "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
     "fno_epi_dx_mma_bf16x3": (0.800936e9 + 0.616677e9) / 167772160,
-    "fno_fwd_tz_tc_bf16x3": (0.6712366e9 + 0.1125819e9) / 167772160,
+    "fno_fwd_tz_mma_bf16x3": (0.671130e9 + 0.111769e9) / 167772160,
 }
 
 
@@ -187,7 +187,7 @@ def roofline_of(name, per_launch_ms, dd, pk, precision):
     tfl = nflops / sec / 1e12
     f_hbm = gbs / pk["hbm_gbs"]
     if "_tc_" in name or "_mma_" in name:
-        # tensor-core kernels (tcgen05 or mma.sync): algorithmic flops against
+        # tensor-core kernels (mma.sync): algorithmic flops against
         # the dense BF16 peak; split BF16 issues 3 (DFT stages) or 6 (1x1
         # stages) products per real multiply-add, which the fraction leaves out
         comp = {"bound": "tensor", "achieved": round(tfl, 2), "peak": pk["bf16_tflops"],

@@ -66,9 +66,9 @@ typedef struct fno_dims {
  *   FNO_BF16X3  split BF16 on the tensor cores: hi + lo with three products
  *               in the DFT stages, three-way splits with six products in the
  *               1x1 and line stages
- * The tensor-core precisions need Nz in {16, 32, 64, 128}, Nt a multiple of 8
- * up to 64 and mt <= 8 (FNO_ERR_UNSUPPORTED otherwise); stages outside the
- * tensor-core tilings fall back to the FP32 kernels. */
+ * The tensor-core precisions need Nz a multiple of 16, Nt a multiple of 8 up
+ * to 64, mt <= 8 and 2 mz <= 64 (FNO_ERR_UNSUPPORTED otherwise); stages
+ * outside the other tensor-core tilings fall back to the FP32 kernels. */
 typedef enum fno_precision {
   FNO_FP32 = 0,
   FNO_TF32 = 1,

@@ -136,7 +136,7 @@ static int check_support(const Dims& d, int precision, int op) {
     return fail(FNO_ERR_INVALID_ARG, "op %d is not an fno_op", op);
   if (is_tc(precision)) {
     char why[256];
-    if (!fwd_tz_tc_supported(d, why, sizeof(why))) return fail(FNO_ERR_UNSUPPORTED, "%s", why);
+    if (!fwd_tz_mma_supported(d, why, sizeof(why))) return fail(FNO_ERR_UNSUPPORTED, "%s", why);
   }
   if (d.Ci > kMaxChannels || d.Co > kMaxChannels)
     return fail(FNO_ERR_UNSUPPORTED, "C_in, C_out must be <= %lld", (long long)kMaxChannels);
@@ -250,8 +250,8 @@ static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2
                         const Tables& T, float2* t1, float2* t2, float2* out, cudaStream_t s,
                         int precision = FNO_FP32, int* err = nullptr) {
   if (is_tc(precision))
-    CK(launch_fwd_tz_tc(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, is_split(precision), precision == FNO_TF32,
-                        err, s));
+    CK(launch_fwd_tz_mma(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, is_split(precision),
+                         precision == FNO_TF32, err, s));
   else
     CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
   CK(line(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, precision, s));

@@ -99,14 +99,6 @@ bool line_mma_supported(int nin, int nout);
 cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int nin, int nout,
                             int64_t inner, const float2* tab, bool split, bool tf32, cudaStream_t s);
 
-// ---- tensor-core path (fno_tc.cu) -------------------------------------------
-// Pruned DFT over t then z on tcgen05 (BF16 or split BF16); same contract as
-// launch_fwd_tz_f32.  err: device word set to nonzero when a bounded wait gives up.
-bool fwd_tz_tc_supported(const Dims& d, char* why, size_t nwhy);
-cudaError_t launch_fwd_tz_tc(const float* in, float2* out, int64_t ncol, const Dims& d,
-                             const float2* ft, const float2* fz, bool split, bool tf32, int* err,
-                             cudaStream_t s);
-
 // ---- layers around the blocks (fno_pointwise.cu) ---------------------------
 // y[b,o,p] = act(sum_i x[b,i,p] w[i,o] + bias[o]) (bias nullable, act 0/1 = none/GELU).
 cudaError_t launch_pointwise_fwd(const float* x, const float* w, const float* bias, float* y,
@@ -122,6 +114,14 @@ int pointwise_max_grid(int Ci, int Co);  // the most rows launch_pointwise_bwd w
 int mse_max_grid();
 cudaError_t launch_mse(const float* y, const float* t, float* dy, int64_t n, float* loss,
                        float* part, cudaStream_t s);
+
+// Pruned DFT over t then z with both stages on mma.sync (fno_mma.cu); same
+// contract as launch_fwd_tz_f32.  err: device word set to nonzero when a
+// bounded wait gives up.
+bool fwd_tz_mma_supported(const Dims& d, char* why, size_t nwhy);
+cudaError_t launch_fwd_tz_mma(const float* in, float2* out, int64_t ncol, const Dims& d,
+                              const float2* ft, const float2* fz, bool split, bool tf32, int* err,
+                              cudaStream_t s);
 
 #ifdef __CUDACC__
 // Launch with the profiling hooks; returns the launch error from the caller.

@@ -42,7 +42,7 @@
 #include <cstdio>
 
 #include "fno_internal.h"
-#include "umma.h"
+#include "tma.h"
 
 namespace fno {
 
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
 
   // TMA destinations must be 128-byte aligned: refuse (uniformly, before any
   // copy is issued) rather than fault if the dynamic shared window is not
-  if ((umma::smem_u32(stg) & 127u) != 0u) {
+  if ((tma::smem_u32(stg) & 127u) != 0u) {
     if (tid == 0 && k.err) atomicExch(k.err, 2);
     return;
   }
@@ -299,9 +299,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
   }
   if (tid == 0) {
     s_abort = 0;
-    umma::mbar_init(&bar[0], 1);
-    umma::mbar_init(&bar[1], 1);
-    umma::fence_mbar_init();
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_mbar_init();
   }
   // t-basis A fragments Tb[t][k2]: k2 < 8 c/N cos (jt = k2), k2 >= 8 -c/N sin (jt = k2 - 8)
   {
@@ -366,10 +366,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
   auto issue = [&](long long bb, long long xyy, int zbb, int buf) {
     if (tid == 0) {
       unsigned char* dst = stg + (size_t)buf * k.SB;
-      umma::fence_proxy_async();
-      umma::mbar_arrive_expect_tx(&bar[buf], (uint32_t)(sizeof(float) * Cl * kP) + bz_bytes);
-      if (Cl > 0) umma::tma_load_2d(dst, &k.tmx, (int)(xyy * k.plane + (long long)zbb * kP), (int)(bb * Cl), &bar[buf]);
-      umma::bulk_g2s(dst + k.BZO, k.bz + (size_t)zbb * k.NZT * k.KZ * 64, bz_bytes, &bar[buf]);
+      tma::fence_proxy_async();
+      tma::mbar_arrive_expect_tx(&bar[buf], (uint32_t)(sizeof(float) * Cl * kP) + bz_bytes);
+      if (Cl > 0) tma::tma_load_2d(dst, &k.tmx, (int)(xyy * k.plane + (long long)zbb * kP), (int)(bb * Cl), &bar[buf]);
+      tma::bulk_g2s(dst + k.BZO, k.bz + (size_t)zbb * k.NZT * k.KZ * 64, bz_bytes, &bar[buf]);
     }
     pending |= 1u << buf;
   };
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
                            : 0.f;
     }
     // this tile's staging buffer (prefetched during the previous tile)
-    if (umma::mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+    if (tma::mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
       phase ^= 1u << buf;
       pending &= ~(1u << buf);
     } else {
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
   if (tid == 0) {
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      if (pending & (1u << q)) (void)umma::mbar_wait(&bar[q], (phase >> q) & 1u);
+      if (pending & (1u << q)) (void)tma::mbar_wait(&bar[q], (phase >> q) & 1u);
   }
 
   if (MODE == EPI_DA) {
@@ -1150,6 +1150,387 @@ cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int ni
                   : launch_line_t<true, false, false>(L, smem, "fno_line_mma_bf16x3", s);
   return kouter ? launch_line_t<false, true, false>(L, smem, "fno_line_mma_bf16", s)
                 : launch_line_t<false, false, false>(L, smem, "fno_line_mma_bf16", s);
+}
+
+}  // namespace fno
+
+// ============================================================================
+// Forward pruned DFT over t then z of every (b, c, x, y) column, both stages on
+// mma.sync in registers (the first half of F_yzt, S_yzt in Alg. 2).
+//
+//   t stage  P_ri[jt][z] = sum_t F_ri[jt][t] X[z][t]        ri = re (cos), im (-sin)
+//   z stage  T[kz][jt]   = sum_z Fz[kz][z] (P_re + i P_im)[jt][z]
+//            Re T = Fz_r P_re - Fz_i P_im,   Im T = Fz_r P_im + Fz_i P_re
+//
+// One warp owns one column at a time.  The t stage is m16n8k16 with the basis
+// as the A operand (rows ri * 8 + jt) and the column as B (k = t, n = z): its C
+// fragments of the n-tiles 2 ks and 2 ks + 1 hold (jt = lane / 4, z = 16 ks +
+// 2 (lane % 4) + {0, 1} and + 8), which is exactly the B fragment (k = z, n =
+// jt) of the z stage's k-step ks -- the two stages chain in registers, with no
+// shared-memory round trip and no TMEM.  The t stage's k slots map to four
+// consecutive t per thread (one float4 of the staged column; the basis
+// fragments use the same map).  The z basis sits in shared memory already in
+// A-fragment order (one 16-byte load per lane and operand part).  Each z
+// k-step accumulates from zero and is added into FP32 totals, so tensor-core
+// accumulation chains stay at six MMAs.
+//
+// Columns arrive by bulk copy (TMA engine) into a ring of S stages (16 KB: G
+// columns, or one column in NCH chunks); warp 0 is the producer, warps
+// 1..kTzWarps take the column units w - 1, w - 1 + kTzWarps, ... in order, so a
+// consumer skips stages: it waits on a stage's barrier only after the producer
+// has published that it issued the stage (see `issued`).  Two CTAs share an SM
+// (two producers measured 1.24 ms against 1.47 ms for one at 128^3 x 32; larger
+// or smaller stages were slower).  Every wait is bounded: on timeout the kernel
+// raises *err, the producer waits (bounded) for its copies in flight, and all
+// warps return.
+// ============================================================================
+namespace fno {
+namespace {
+
+constexpr int kTzWarps = 8;                      // consumer warps
+constexpr int kTzThreads = 32 * (kTzWarps + 1);
+constexpr int kTzKT = 4;                         // t-stage k-steps (Nt <= 64)
+constexpr long long kTzWait = 4000000000LL;      // about 2 s of SM clocks
+
+struct TzM {
+  const float* in;     // [ncol][Nz][Nt]
+  float2* out;         // [ncol][Jz][Jt]
+  const float2* Ft;    // [Jt][Nt]  (cos, -sin) * scale
+  const float2* Fz;    // [Jz][Nz]  (cos, -sin)
+  int* err;
+  long long ncol, nunits;   // units: G whole columns, or one column in NCH chunks
+  int Nz, Nt, Jz, Jt, KT, KZ, G, S, NCH, zc;
+  uint32_t col_floats, o_fz, o_ring, stage_bytes, o_bar;
+};
+
+// Wait (bounded) until the producer has issued stage g; false on timeout or abort.
+__device__ __forceinline__ bool tz_wait_issued(volatile int* issued, volatile int* abort_flag,
+                                               int g) {
+  if (*issued > g) return true;
+  const long long t0 = clock64();
+  while (*issued <= g) {
+    if (*abort_flag || clock64() - t0 > kTzWait) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// CTAs per SM: two producers per SM measured faster than one; four z m-tiles
+// need the registers of a whole SM.
+__host__ __device__ constexpr int tz_ctas(int mz) { return mz <= 2 ? 2 : 1; }
+
+template <int MZ, bool SPLIT, bool TF>
+__global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __grid_constant__ TzM p) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int S = p.S;
+  uint4* fzf = reinterpret_cast<uint4*>(sm + p.o_fz);  // [MZ][KZ][4 parts][32 lanes]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + p.o_bar);
+  uint64_t* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  // stages issued so far: a consumer waits on stage g's barrier only once the
+  // producer has issued g.  Issuing g needed stage g - S consumed (so landed),
+  // so the slot's barrier is then exactly in stage g's phase and the parity
+  // test cannot match an older, still open phase.
+  volatile int* issued = abort_flag + 1;
+
+  // z basis in A-fragment order: parts (re hi, re lo, im hi, im lo); rows kz,
+  // cols z; a0 = (kz g8, z 2 t4 + {0,1}), a1 = (kz g8 + 8, ...), a2, a3 at z + 8
+  for (int e = tid; e < MZ * p.KZ * 32; e += kTzThreads) {
+    const int ln = e & 31, ks = (e >> 5) % p.KZ, mt = (e >> 5) / p.KZ;
+    const int r0 = 16 * mt + (ln >> 2), c0 = 16 * ks + 2 * (ln & 3);
+    auto F = [&](int kz, int z, int im) -> float {
+      if (kz >= p.Jz) return 0.f;
+      const float2 f = p.Fz[(long long)kz * p.Nz + z];
+      return rnd<TF>(im ? f.y : f.x);
+    };
+#pragma unroll
+    for (int im = 0; im < 2; ++im) {
+      uint32_t h[4], l[4];
+      split2(F(r0, c0, im), F(r0, c0 + 1, im), h[0], l[0]);
+      split2(F(r0 + 8, c0, im), F(r0 + 8, c0 + 1, im), h[1], l[1]);
+      split2(F(r0, c0 + 8, im), F(r0, c0 + 9, im), h[2], l[2]);
+      split2(F(r0 + 8, c0 + 8, im), F(r0 + 8, c0 + 9, im), h[3], l[3]);
+      const int base = ((mt * p.KZ + ks) * 4 + 2 * im) * 32 + ln;
+      fzf[base] = make_uint4(h[0], h[1], h[2], h[3]);
+      fzf[base + 32] = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tma::mbar_init(&full[s], 1);
+      tma::mbar_init(&empty[s], 1);
+    }
+    *abort_flag = 0;
+    *issued = 0;
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+
+  const long long nmine = (p.nunits > blockIdx.x)
+                              ? (p.nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      long long g = 0;
+      const long long nstages = nmine * p.NCH;
+      for (; g < nstages; ++g) {
+        const int s = (int)(g % S);
+        if (g >= S && !tma::mbar_wait(&empty[s], (uint32_t)(((g - S) / S) & 1), kTzWait)) {
+          atomicExch(p.err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        if (*abort_flag) break;
+        const long long u = blockIdx.x + (long long)((int)g / p.NCH) * gridDim.x;
+        const int ch = (int)g % p.NCH;
+        const long long c0 = u * p.G;
+        const long long nc = min((long long)p.G, p.ncol - c0);
+        const uint32_t bytes = (p.NCH > 1) ? (uint32_t)(p.zc * p.Nt * 4)
+                                           : (uint32_t)(nc * p.col_floats * 4);
+        const float* src = p.in + c0 * p.col_floats + (long long)ch * p.zc * p.Nt;
+        tma::mbar_arrive_expect_tx(&full[s], bytes);
+        tma::bulk_g2s(sm + p.o_ring + (size_t)s * p.stage_bytes, src, bytes, &full[s]);
+        __threadfence_block();
+        *issued = (int)g + 1;
+      }
+      // every copy this CTA started has landed before its shared memory is released
+      for (long long q = (g > S ? g - S : 0); q < g; ++q)
+        (void)tma::mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), kTzWait);
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int cw = warp - 1;
+  // t basis A fragments (rows ri * 8 + jt, k slots <-> t = 16 ks + 4 t4 + {0,1} / {2,3})
+  uint32_t fth[kTzKT][4], ftl[kTzKT][4];
+#pragma unroll
+  for (int ks = 0; ks < kTzKT; ++ks) {
+    const int t0 = 16 * ks + 4 * t4;
+    auto F = [&](int ri, int t) -> float {
+      if (g8 >= p.Jt || t >= p.Nt || ks >= p.KT) return 0.f;
+      const float2 f = p.Ft[(long long)g8 * p.Nt + t];
+      return rnd<TF>(ri ? f.y : f.x);
+    };
+    split2(F(0, t0), F(0, t0 + 1), fth[ks][0], ftl[ks][0]);
+    split2(F(1, t0), F(1, t0 + 1), fth[ks][1], ftl[ks][1]);
+    split2(F(0, t0 + 2), F(0, t0 + 3), fth[ks][2], ftl[ks][2]);
+    split2(F(1, t0 + 2), F(1, t0 + 3), fth[ks][3], ftl[ks][3]);
+  }
+  const int Nt = p.Nt;
+  const int kzc = p.zc / 16;  // z k-steps per staged chunk
+  bool ok = true;
+  for (int cu = cw; cu < (int)nmine && ok; cu += kTzWarps) {
+    const long long u = blockIdx.x + (long long)cu * gridDim.x;
+    const long long c0 = u * p.G;
+    const int nc = (int)min((long long)p.G, p.ncol - c0);
+    for (int cl = 0; cl < nc && ok; ++cl) {
+      float tre[MZ][4], tim[MZ][4];
+#pragma unroll
+      for (int mt = 0; mt < MZ; ++mt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tre[mt][q] = tim[mt][q] = 0.f;
+      for (int ch = 0; ch < p.NCH; ++ch) {
+        // the stage of this chunk (a whole unit of G columns when NCH = 1)
+        const int g = cu * p.NCH + ch;
+        const int s = g % S;
+        if ((p.NCH > 1 || cl == 0) &&
+            (!tz_wait_issued(issued, abort_flag, g) ||
+             !tma::mbar_wait(&full[s], (uint32_t)((g / S) & 1), kTzWait) || *abort_flag)) {
+          if (lane == 0) {
+            atomicExch(p.err, 1);
+            *abort_flag = 1;
+          }
+          ok = false;
+          break;
+        }
+        const float* xs = reinterpret_cast<const float*>(sm + p.o_ring + (size_t)s * p.stage_bytes) +
+                          (size_t)cl * p.col_floats;
+        for (int kl = 0; kl < kzc; ++kl) {
+          const int kz = ch * kzc + kl;
+          // t stage of z = 16 kz .. 16 kz + 15 (two n-tiles; staged rows 16 kl ..)
+          float pc[2][4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pc[h][q] = 0.f;
+            const float* row = xs + (size_t)(16 * kl + 8 * h + g8) * Nt;
+#pragma unroll
+            for (int ks = 0; ks < kTzKT; ++ks) {
+              if (ks < p.KT) {
+                const int tt = 16 * ks + 4 * t4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tt < Nt) v = *reinterpret_cast<const float4*>(row + tt);
+                uint32_t bh0, bl0, bh1, bl1;
+                split2(rnd<TF>(v.x), rnd<TF>(v.y), bh0, bl0);
+                split2(rnd<TF>(v.z), rnd<TF>(v.w), bh1, bl1);
+                if (SPLIT) {
+                  mma16(pc[h], ftl[ks][0], ftl[ks][1], ftl[ks][2], ftl[ks][3], bh0, bh1);
+                  mma16(pc[h], fth[ks][0], fth[ks][1], fth[ks][2], fth[ks][3], bl0, bl1);
+                }
+                mma16(pc[h], fth[ks][0], fth[ks][1], fth[ks][2], fth[ks][3], bh0, bh1);
+              }
+            }
+          }
+          // z stage k-step kz: B fragments straight from the t-stage accumulators
+          uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
+          split2(rnd<TF>(pc[0][0]), rnd<TF>(pc[0][1]), rh0, rl0);  // P_re, z + 0..7
+          split2(rnd<TF>(pc[1][0]), rnd<TF>(pc[1][1]), rh1, rl1);  // P_re, z + 8..15
+          split2(rnd<TF>(pc[0][2]), rnd<TF>(pc[0][3]), ih0, il0);  // P_im
+          split2(rnd<TF>(pc[1][2]), rnd<TF>(pc[1][3]), ih1, il1);
+          const uint32_t nh0 = ih0 ^ 0x80008000u, nh1 = ih1 ^ 0x80008000u;  // -P_im
+          const uint32_t nl0 = il0 ^ 0x80008000u, nl1 = il1 ^ 0x80008000u;
+#pragma unroll
+          for (int mt = 0; mt < MZ; ++mt) {
+            const int base = ((mt * p.KZ + kz) * 4) * 32 + lane;
+            const uint4 arh = fzf[base], arl = fzf[base + 32];
+            const uint4 aih = fzf[base + 64], ail = fzf[base + 96];
+            float dr[4] = {0.f, 0.f, 0.f, 0.f}, di[4] = {0.f, 0.f, 0.f, 0.f};
+            if (SPLIT) {
+              mma16(dr, arl.x, arl.y, arl.z, arl.w, rh0, rh1);
+              mma16(dr, arh.x, arh.y, arh.z, arh.w, rl0, rl1);
+              mma16(dr, ail.x, ail.y, ail.z, ail.w, nh0, nh1);
+              mma16(dr, aih.x, aih.y, aih.z, aih.w, nl0, nl1);
+              mma16(di, arl.x, arl.y, arl.z, arl.w, ih0, ih1);
+              mma16(di, arh.x, arh.y, arh.z, arh.w, il0, il1);
+              mma16(di, ail.x, ail.y, ail.z, ail.w, rh0, rh1);
+              mma16(di, aih.x, aih.y, aih.z, aih.w, rl0, rl1);
+            }
+            mma16(dr, arh.x, arh.y, arh.z, arh.w, rh0, rh1);
+            mma16(dr, aih.x, aih.y, aih.z, aih.w, nh0, nh1);
+            mma16(di, arh.x, arh.y, arh.z, arh.w, ih0, ih1);
+            mma16(di, aih.x, aih.y, aih.z, aih.w, rh0, rh1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              tre[mt][q] += dr[q];
+              tim[mt][q] += di[q];
+            }
+          }
+        }
+        if (p.NCH > 1) {  // the chunk has been read
+          __syncwarp();
+          if (lane == 0) tma::mbar_arrive(&empty[s]);
+        }
+      }
+      if (!ok) break;
+      // T[col][kz][jt]: rows kz = 16 mt + g8 (+8), cols jt = 2 t4 + {0, 1}
+      float2* oc = p.out + (c0 + cl) * (long long)(p.Jz * p.Jt);
+#pragma unroll
+      for (int mt = 0; mt < MZ; ++mt)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int kz = 16 * mt + g8 + 8 * hh;
+          if (kz >= p.Jz) continue;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int jt = 2 * t4 + e;
+            if (jt < p.Jt) oc[kz * p.Jt + jt] = make_float2(tre[mt][2 * hh + e], tim[mt][2 * hh + e]);
+          }
+        }
+    }
+    if (ok && p.NCH == 1) {  // every column of the stage has been read
+      __syncwarp();
+      if (lane == 0) tma::mbar_arrive(&empty[cu % S]);
+    }
+  }
+}
+
+}  // namespace
+
+// plan: stage columns G (a stage holds at least 8 KB), ring depth S, offsets
+static bool tz_mma_plan(const Dims& d, TzM& k, size_t& smem) {
+  k.Nz = (int)d.Nz;
+  k.Nt = (int)d.Nt;
+  k.Jz = (int)d.Jz;
+  k.Jt = (int)d.Jt;
+  k.KT = (int)((d.Nt + 15) / 16);
+  k.KZ = (int)(d.Nz / 16);
+  const int MZ = (int)((d.Jz + 15) / 16);
+  k.col_floats = (uint32_t)(d.Nz * d.Nt);
+  const size_t colb = 4 * (size_t)k.col_floats;
+  const size_t target = 16 * 1024;  // stage bytes (fewer, larger bulk copies measured faster)
+  if (colb > target) {
+    // one column in NCH chunks of zc rows (zc a multiple of 16 dividing Nz)
+    int nch = (int)((colb + target - 1) / target);
+    while (nch < k.KZ && (k.KZ % nch) != 0) ++nch;
+    k.NCH = std::min(nch, k.KZ);
+    k.zc = (int)(d.Nz / k.NCH);
+    k.G = 1;
+    k.stage_bytes = (uint32_t)(4 * (size_t)k.zc * d.Nt);
+  } else {
+    k.NCH = 1;
+    k.zc = (int)d.Nz;
+    k.G = (int)std::max<size_t>(1, target / colb);
+    k.stage_bytes = (uint32_t)(k.G * colb);
+  }
+  const size_t fzb = (size_t)(MZ <= 1 ? 1 : MZ <= 2 ? 2 : 4) * k.KZ * 4 * 32 * 16;
+  k.o_fz = 0;
+  k.o_ring = (uint32_t)((fzb + 127) / 128 * 128);
+  const size_t budget = 227 * 1024 / tz_ctas(MZ) - k.o_ring - 1024;
+  k.S = (int)std::min<size_t>(32, budget / k.stage_bytes);
+  if (k.S < 2) return false;
+  k.o_bar = (uint32_t)(k.o_ring + (size_t)k.S * k.stage_bytes);
+  smem = k.o_bar + 16 * (size_t)k.S + 16;
+  return smem <= 227 * 1024;
+}
+
+bool fwd_tz_mma_supported(const Dims& d, char* why, size_t nwhy) {
+  const char* r = nullptr;
+  if (d.Nt % 8 != 0 || d.Nt > 64)
+    r = "the tensor-core t stage needs Nt a multiple of 8 up to 64";
+  else if (d.Nz % 16 != 0)
+    r = "the tensor-core z stage needs Nz a multiple of 16";
+  else if (d.Jt > 8)
+    r = "the tensor-core t stage needs mt <= 8";
+  else if (d.Jz > 64)
+    r = "the tensor-core z stage needs 2 mz <= 64";
+  if (!r) {
+    TzM k{};
+    size_t smem = 0;
+    if (!tz_mma_plan(d, k, smem)) r = "a column of Nz x Nt floats does not fit the staging ring";
+  }
+  if (r && why) snprintf(why, nwhy, "%s", r);
+  return r == nullptr;
+}
+
+template <int MZ, bool SPLIT, bool TF>
+static cudaError_t launch_tz_t(const TzM& k, size_t smem, const char* name, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_tz_mma<MZ, SPLIT, TF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid =
+      (int)std::max<long long>(1, std::min<long long>((long long)tz_ctas(MZ) * sm_count(), k.nunits));
+  FNO_LAUNCH(name, (k_fwd_tz_mma<MZ, SPLIT, TF>), grid, kTzThreads, smem, s, k);
+  return cudaSuccess;
+}
+
+template <int MZ>
+static cudaError_t launch_tz_m(const TzM& k, size_t smem, bool split, bool tf32, cudaStream_t s) {
+  if (tf32) return launch_tz_t<MZ, true, true>(k, smem, "fno_fwd_tz_mma_tf32", s);
+  if (split) return launch_tz_t<MZ, true, false>(k, smem, "fno_fwd_tz_mma_bf16x3", s);
+  return launch_tz_t<MZ, false, false>(k, smem, "fno_fwd_tz_mma_bf16", s);
+}
+
+cudaError_t launch_fwd_tz_mma(const float* in, float2* out, int64_t ncol, const Dims& d,
+                              const float2* ft, const float2* fz, bool split, bool tf32, int* err,
+                              cudaStream_t s) {
+  if (ncol <= 0) return cudaSuccess;
+  TzM k{};
+  size_t smem = 0;
+  if (!tz_mma_plan(d, k, smem)) return cudaErrorInvalidValue;
+  k.in = in;
+  k.out = out;
+  k.Ft = ft;
+  k.Fz = fz;
+  k.err = err;
+  k.ncol = ncol;
+  k.nunits = (ncol + k.G - 1) / k.G;
+  const int MZ = (int)((d.Jz + 15) / 16);
+  if (MZ <= 1) return launch_tz_m<1>(k, smem, split, tf32, s);
+  if (MZ <= 2) return launch_tz_m<2>(k, smem, split, tf32, s);
+  return launch_tz_m<4>(k, smem, split, tf32, s);
 }
 
 }  // namespace fno
