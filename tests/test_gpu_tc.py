@@ -73,6 +73,11 @@ TC_CASES = [
     # covered by 1 -> 2 and 2 -> 1 channels instead
     (Dims(2, 1, 2, 4, 6, 32, 16, 2, 3, 5, 8), "one input channel, mt = Nt/2"),
     (Dims(2, 2, 1, 4, 6, 32, 16, 2, 3, 5, 8), "one output channel, mt = Nt/2"),
+    # forward t,z kernel shapes: a 32 KB column staged in two chunks, three z
+    # m-tiles on a non-power-of-two Nz, and a half-empty (masked) t k-step
+    (Dims(1, 3, 3, 4, 4, 128, 64, 1, 1, 5, 8), "Nz=128, Nt=64: each column in two staged chunks"),
+    (Dims(1, 2, 3, 4, 4, 96, 16, 1, 2, 20, 4), "Nz=96, 2mz=40: three z m-tiles"),
+    (Dims(2, 2, 2, 4, 4, 32, 24, 1, 1, 4, 6), "Nt=24: the second t k-step half masked"),
 ]
 
 
