@@ -1,8 +1,9 @@
 #!/usr/bin/env python3
 """Benchmark of the 4-D spectral FNO block, forward + backward, on one GB300.
 
-One step = fno_block_fwd + fno_block_bwd (recompute of the forward spectrum
-inside the backward: per-block activation checkpointing) over one batch of the
+One step = fno_block_fwd + fno_block_bwd_saved (per-block activation
+checkpointing: between the passes only the block input and the forward's
+truncated spectra, kept in the workspace, are held) over one batch of the
 CO2-flow-like block workload: B=1, width 20, grid 128x128x128 (~2.1 M cells)
 x 32 time steps, kept modes 12/12/8/8, input a seeded anisotropic smooth
 Gaussian random field (correlation 20x20x4 cells, 8 steps), upstream gradient
@@ -556,15 +557,16 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sh = int(stream.cuda_stream)
 
-    def step_of(prec):
+    def step_of(prec, saved=True):
+        """fno_block_fwd + the backward; saved: reuse the forward's spectra from ws."""
         pc = ops.precision_code(prec)
+        bwd = _lib.fno_block_bwd_saved if saved else _lib.fno_block_bwd
 
         def st():
             _lib.fno_block_fwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
                                z.data_ptr(), ws.data_ptr(), nws, sh)
-            _lib.fno_block_bwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
-                               dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(),
-                               db.data_ptr(), ws.data_ptr(), nws, sh)
+            bwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(), dz.data_ptr(),
+                dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(), db.data_ptr(), ws.data_ptr(), nws, sh)
         return st
 
     step = step_of(args.precision)
@@ -577,9 +579,10 @@ def main():
         def st():
             _lib.fno_block_fwd(d, pc, xb.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
                                zb.data_ptr(), ws.data_ptr(), nws, sh)
-            _lib.fno_block_bwd(d, pc, xb.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
-                               dzb.data_ptr(), dxb.data_ptr(), dwb.data_ptr(), dwlb.data_ptr(),
-                               dbb.data_ptr(), ws.data_ptr(), nws, sh)
+            _lib.fno_block_bwd_saved(d, pc, xb.data_ptr(), w.data_ptr(), wl.data_ptr(),
+                                     bias.data_ptr(), dzb.data_ptr(), dxb.data_ptr(),
+                                     dwb.data_ptr(), dwlb.data_ptr(), dbb.data_ptr(),
+                                     ws.data_ptr(), nws, sh)
         return st
 
     def barrier():
@@ -611,6 +614,20 @@ def main():
     ms = reduce_step_time(e0.elapsed_time(e1) / args.steps, dist, dev)
     units = B * C * Ng
     value = whole_job_value(units, world, ms)
+
+    # the same step with the backward recomputing the forward spectra from x
+    step_rc = step_of(args.precision, saved=False)
+    for _ in range(2):
+        step_rc()
+    barrier()
+    e4 = torch.cuda.Event(enable_timing=True)
+    e5 = torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for _ in range(args.steps):
+        step_rc()
+    e5.record(stream)
+    barrier()
+    ms_rc = reduce_step_time(e4.elapsed_time(e5) / args.steps, dist, dev)
 
     # ---- end to end: pinned host inputs -> C ABI -> host results ----
     # Every step copies its inputs from pinned host memory and its results back.
@@ -701,7 +718,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "B": B, "C_in": C, "C_out": C,
                        "grid": [Nx, Ny, Nz, Nt], "modes": [mx, my, mz, mt], "precision": args.precision,
-                       "step": "fno_block_fwd + fno_block_bwd (backward recomputes the forward spectrum)",
+                       "step": "fno_block_fwd + fno_block_bwd_saved (the backward reuses the "
+                               "forward's truncated spectra, kept in the workspace)",
+                       "recompute_ms_per_step": round(ms_rc, 4),
                        "l2": "inputs larger than L2 (5.4 GB per tensor); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -125,6 +125,24 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
                   const float* w_lin, const float* bias, const float* dz, float* dx, float* dw,
                   float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream);
 
+/* Block backward that reuses the forward's spectra instead of recomputing them.
+ * After fno_block_fwd the workspace holds the input's kept spectrum Xh and the
+ * inverse x, y partial of the output spectrum (together about 0.35 GB at width
+ * 20 on 128^3 x 32, against 5.4 GB for the input); this call takes them from
+ * there and runs only the adjoint chain, computing exactly what fno_block_bwd
+ * computes.  Per-block checkpointing still holds: only the block input and
+ * these truncated spectra live between the passes.
+ * Contract: ws (and ws_bytes, sized for FNO_OP_BLOCK_BWD) is the workspace of
+ * the last fno_block_fwd call made with it, with the same dims, precision, x
+ * and w, and no other call has used ws since; x and w are unchanged.  The
+ * library records which forward call left its state in each workspace (host
+ * bookkeeping only) and refuses with FNO_ERR_INVALID_ARG when the record does
+ * not match; it cannot see writes to x or w made by the caller. */
+int fno_block_bwd_saved(const fno_dims* dims, int precision, const float* x, const float* w,
+                        const float* w_lin, const float* bias, const float* dz, float* dx,
+                        float* dw, float* dw_lin, float* db, void* ws, size_t ws_bytes,
+                        void* stream);
+
 /* Status a previous call left in its workspace: waits for `stream`, then returns
  * FNO_OK, FNO_ERR_TIMEOUT when one of that call's bounded device-side waits
  * (tensor-core pipeline barriers) gave up and the kernel returned early, or

@@ -24,7 +24,7 @@ EXPORTS = (
     "fno_block_bwd", "fno_last_error", "fno_version", "fno_launch_count", "fno_profile_start",
     "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static", "fno_workspace_status", "fno_last_status",
     "fno_pointwise_fwd", "fno_pointwise_workspace_bytes", "fno_pointwise_bwd",
-    "fno_mse_workspace_bytes", "fno_mse_loss",
+    "fno_mse_workspace_bytes", "fno_mse_loss", "fno_block_bwd_saved",
 )
 FNO_ACT_NONE, FNO_ACT_GELU = 0, 1
 FNO_STATIC_SCRATCH_BYTES = 16 << 20
@@ -74,7 +74,9 @@ def load(build_if_needed: bool = True):
         lib.fno_spectral_fwd_static.argtypes = [dp, ci, vp, vp, vp, vp]
         lib.fno_spectral_fwd_static.restype = ci
         lib.fno_block_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
-        for f in (lib.fno_spectral_fwd, lib.fno_spectral_bwd, lib.fno_block_fwd, lib.fno_block_bwd):
+        lib.fno_block_bwd_saved.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        for f in (lib.fno_spectral_fwd, lib.fno_spectral_bwd, lib.fno_block_fwd, lib.fno_block_bwd,
+                  lib.fno_block_bwd_saved):
             f.restype = ci
         lib.fno_workspace_status.argtypes = [vp, vp]
         lib.fno_workspace_status.restype = ci
@@ -153,6 +155,13 @@ def fno_block_bwd(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws
                   stream=0):
     _check(load().fno_block_bwd(ctypes.byref(dims), int(precision), x, w, w_lin, bias, dz, dx, dw,
                                 dw_lin, db, ws, ws_bytes, stream))
+
+
+def fno_block_bwd_saved(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws, ws_bytes,
+                        stream=0):
+    """fno_block_bwd reusing the spectra the last fno_block_fwd left in ws."""
+    _check(load().fno_block_bwd_saved(ctypes.byref(dims), int(precision), x, w, w_lin, bias, dz,
+                                      dx, dw, dw_lin, db, ws, ws_bytes, stream))
 
 
 def fno_workspace_status(ws, stream=0):

@@ -321,6 +321,48 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   return FNO_OK;
 }
 
+// ---- forward state kept in a workspace ---------------------------------------
+// After fno_block_fwd the workspace holds the block input's kept spectrum X̂ and
+// the inverse x, y partial U1 of the output spectrum; fno_block_bwd_saved
+// reuses them instead of recomputing.  The library remembers, per workspace,
+// which forward call left that state (host-side bookkeeping: no device sync);
+// any other call on the workspace forgets it.
+struct SavedFwd {
+  const void* ws;
+  const float* x;
+  const float* w;
+  fno_dims dims;
+  int precision;
+};
+static std::mutex g_saved_mu;
+static std::vector<SavedFwd> g_saved;
+static const size_t kSavedMax = 4096;
+
+static void saved_forget(const void* ws) {
+  std::lock_guard<std::mutex> lk(g_saved_mu);
+  for (size_t i = 0; i < g_saved.size(); ++i)
+    if (g_saved[i].ws == ws) {
+      g_saved.erase(g_saved.begin() + (long)i);
+      return;
+    }
+}
+static void saved_set(const void* ws, const float* x, const float* w, const fno_dims& dims,
+                      int precision) {
+  saved_forget(ws);
+  std::lock_guard<std::mutex> lk(g_saved_mu);
+  if (g_saved.size() >= kSavedMax) g_saved.erase(g_saved.begin());
+  g_saved.push_back(SavedFwd{ws, x, w, dims, precision});
+}
+static bool saved_match(const void* ws, const float* x, const float* w, const fno_dims& dims,
+                        int precision) {
+  std::lock_guard<std::mutex> lk(g_saved_mu);
+  for (const SavedFwd& r : g_saved)
+    if (r.ws == ws)
+      return r.x == x && r.w == w && r.precision == precision &&
+             std::memcmp(&r.dims, &dims, sizeof(fno_dims)) == 0;
+  return false;
+}
+
 // ---- layers around the blocks (Alg. 1) --------------------------------------
 static int to_pw(const fno_pw_dims* pd, int64_t* B, int* Ci, int* Co, int64_t* P) {
   if (!pd) return fail(FNO_ERR_INVALID_ARG, "dims is NULL");
@@ -363,6 +405,7 @@ int fno_spectral_fwd(const fno_dims* dims, int precision, const float* x, const 
   Dims d;
   int rc = to_dims(dims, &d);
   if (rc) return rc;
+  saved_forget(ws);
   return forward_common(d, precision, FNO_OP_SPECTRAL_FWD, x, w, nullptr, nullptr, y, ws,
                         ws_bytes, (cudaStream_t)stream);
 }
@@ -373,8 +416,11 @@ int fno_block_fwd(const fno_dims* dims, int precision, const float* x, const flo
   Dims d;
   int rc = to_dims(dims, &d);
   if (rc) return rc;
-  return forward_common(d, precision, FNO_OP_BLOCK_FWD, x, w, w_lin, bias, z, ws, ws_bytes,
-                        (cudaStream_t)stream);
+  saved_forget(ws);
+  rc = forward_common(d, precision, FNO_OP_BLOCK_FWD, x, w, w_lin, bias, z, ws, ws_bytes,
+                      (cudaStream_t)stream);
+  if (rc == FNO_OK && d.B > 0) saved_set(ws, x, w, *dims, precision);
+  return rc;
 }
 
 int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
@@ -384,6 +430,7 @@ int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const 
   int rc = to_dims(dims, &d);
   if (rc) return rc;
   const int op = FNO_OP_SPECTRAL_BWD;
+  saved_forget(ws);
   if ((rc = check_support(d, precision, op))) return rc;
   const Layout L = layout(d, op);
   if ((rc = check_ws(ws, ws_bytes, L))) return rc;
@@ -427,9 +474,10 @@ int fno_spectral_bwd(const fno_dims* dims, int precision, const float* x, const 
   return FNO_OK;
 }
 
-int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
-                  const float* w_lin, const float* bias, const float* dz, float* dx, float* dw,
-                  float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream) {
+static int block_bwd_impl(const fno_dims* dims, int precision, const float* x, const float* w,
+                          const float* w_lin, const float* bias, const float* dz, float* dx,
+                          float* dw, float* dw_lin, float* db, void* ws, size_t ws_bytes,
+                          void* stream, bool saved) {
   Dims d;
   int rc = to_dims(dims, &d);
   if (rc) return rc;
@@ -465,11 +513,18 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   const float2* wc = reinterpret_cast<const float2*>(w);
 
   int* err = reinterpret_cast<int*>(base + L.err);
+  if (saved && !saved_match(ws, x, w, *dims, precision))
+    return fail(FNO_ERR_INVALID_ARG,
+                "the workspace does not hold the state of an fno_block_fwd call with these "
+                "dims, precision, x and w");
+  saved_forget(ws);  // the steps below overwrite the forward state
   CK(launch_tables(d, T, err, s));
-  // recompute the forward spectrum and the spectral partial U1 of the output
-  if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
-  CK(launch_mix_f32(d, xh, wc, yh, s));
-  if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
+  if (!saved) {
+    // recompute the forward spectrum and the spectral partial U1 of the output
+    if ((rc = spectrum_f32(d, d.Ci, x, T.Ft, T, t1, t2, xh, s, precision, err))) return rc;
+    CK(launch_mix_f32(d, xh, wc, yh, s));
+    if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
+  }
   // dA = dz GELU'(A) with the partial sums of dW_lin and db
   EpiArgs a{};
   a.mode = EPI_DA;
@@ -508,6 +563,21 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
   q.w_sc = (int)d.Co;
   CK(epilogue(d, q, precision, base, L, err, nullptr, s));
   return FNO_OK;
+}
+
+int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const float* w,
+                  const float* w_lin, const float* bias, const float* dz, float* dx, float* dw,
+                  float* dw_lin, float* db, void* ws, size_t ws_bytes, void* stream) {
+  return block_bwd_impl(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws, ws_bytes,
+                        stream, false);
+}
+
+int fno_block_bwd_saved(const fno_dims* dims, int precision, const float* x, const float* w,
+                        const float* w_lin, const float* bias, const float* dz, float* dx,
+                        float* dw, float* dw_lin, float* db, void* ws, size_t ws_bytes,
+                        void* stream) {
+  return block_bwd_impl(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws, ws_bytes,
+                        stream, true);
 }
 
 size_t fno_pointwise_workspace_bytes(const fno_pw_dims* dims) {

@@ -127,7 +127,9 @@ def block_fwd(x, w, w_lin, bias, modes, precision="fp32", ws=None):
     return z
 
 
-def block_bwd(x, w, w_lin, bias, dz, modes, precision="fp32", ws=None):
+def block_bwd(x, w, w_lin, bias, dz, modes, precision="fp32", ws=None, saved=False):
+    """Block backward.  saved=True reuses the spectra the last block_fwd left in ws
+    (the workspace of that call, sized for OP_BLOCK_BWD) instead of recomputing them."""
     x = _req(x, "x")
     Ci, Co = x.shape[1], w.shape[1]
     w = _req(w, "w", _wshape(Ci, Co, modes))
@@ -141,10 +143,13 @@ def block_bwd(x, w, w_lin, bias, dz, modes, precision="fp32", ws=None):
     dwl = torch.empty_like(w_lin)
     db = torch.empty_like(bias)
     if ws is None:
+        if saved:
+            raise ValueError("saved=True needs the workspace of the forward call")
         ws = workspace(d, p, OP_BLOCK_BWD, x.device)
-    _lib.fno_block_bwd(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(),
-                       dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(), db.data_ptr(),
-                       ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+    fn = _lib.fno_block_bwd_saved if saved else _lib.fno_block_bwd
+    fn(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(), dz.data_ptr(),
+       dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(), db.data_ptr(), ws.data_ptr(), ws.numel(),
+       _stream_handle(x.device))
     _status(ws, x.device)
     return dx, dw, dwl, db
 
@@ -169,19 +174,35 @@ class SpectralConv4dFn(torch.autograd.Function):
 
 
 class FNOBlock4dFn(torch.autograd.Function):
-    """z = GELU(S(x; w) + w_lin^T x + bias).  Only x is kept for the backward."""
+    """z = GELU(S(x; w) + w_lin^T x + bias).
+
+    Between the passes the block keeps its input and the forward's workspace,
+    which holds the truncated spectra (X̂ and the inverse x, y partial U1, a
+    small fraction of x); the backward reuses them.  A second backward through
+    the same graph finds the workspace spent and recomputes the spectra.
+    """
 
     @staticmethod
     def forward(ctx, x, w, w_lin, bias, modes, precision="fp32"):
         ctx.modes = tuple(int(m) for m in modes)
         ctx.precision = precision
         ctx.save_for_backward(x, w, w_lin, bias)
-        return block_fwd(x, w, w_lin, bias, ctx.modes, precision)
+        x = _req(x, "x")
+        d = dims_of(x, int(w.shape[1]), ctx.modes)
+        ctx.ws = workspace(d, precision, OP_BLOCK_BWD, x.device)
+        return block_fwd(x, w, w_lin, bias, ctx.modes, precision, ws=ctx.ws)
 
     @staticmethod
     def backward(ctx, dz):
         x, w, w_lin, bias = ctx.saved_tensors
-        dx, dw, dwl, db = block_bwd(x, w, w_lin, bias, dz.contiguous(), ctx.modes, ctx.precision)
+        dz = dz.contiguous()
+        try:
+            out = block_bwd(x, w, w_lin, bias, dz, ctx.modes, ctx.precision, ws=ctx.ws, saved=True)
+        except _lib.FnoError as e:
+            if e.status != -1:
+                raise
+            out = block_bwd(x, w, w_lin, bias, dz, ctx.modes, ctx.precision)
+        dx, dw, dwl, db = out
         return dx, dw, dwl, db, None, None
 
 

@@ -17,6 +17,10 @@ Two ways to run it, both marshalling only (every step is a libfno kernel):
   through the C ABI with preallocated checkpoints, gradients and workspaces: no
   autograd bookkeeping and no allocation inside the pass, so it can be timed
   or captured as it stands.
+
+In both, each block's forward workspace carries its truncated spectra to the
+block's backward, which reuses them (``fno_block_bwd_saved``) instead of
+recomputing them from the checkpointed input.
 """
 from __future__ import annotations
 
@@ -129,7 +133,9 @@ class StackRunner:
         self.bd = _lib.make_dims(self.B, W, W, *self.grid, mx, my, mz, mt)
         nb = max(_lib.fno_workspace_bytes(self.bd, self.prec, ops.OP_BLOCK_FWD),
                  _lib.fno_workspace_bytes(self.bd, self.prec, ops.OP_BLOCK_BWD))
-        self.ws_block = torch.empty(nb, dtype=torch.uint8, device=dev)
+        # one workspace per block: it carries the block's truncated spectra from
+        # the forward to the backward (fno_block_bwd_saved)
+        self.ws_block = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(self.L)]
         self.ed = _lib.make_pw_dims(self.B, self.c_in, W, self.P)
         self.dd = _lib.make_pw_dims(self.B, W, Co, self.P)
         npw = max(_lib.fno_pointwise_workspace_bytes(self.ed),
@@ -139,7 +145,7 @@ class StackRunner:
         self.ws_mse = torch.empty(nm, dtype=torch.uint8, device=dev)
 
     def bytes_held(self) -> int:
-        ts = self.h + [self.y, self.dy, self.loss, self.ws_block, self.ws_pw, self.ws_mse] + self.g
+        ts = self.h + [self.y, self.dy, self.loss, self.ws_pw, self.ws_mse] + self.g + self.ws_block
         return int(sum(t.numel() * t.element_size() for t in ts))
 
     def _check_io(self, x0, target=None):
@@ -158,11 +164,11 @@ class StackRunner:
         p = self.p
         _lib.fno_pointwise_fwd(self.ed, _lib.FNO_ACT_GELU, x0.data_ptr(), p["enc_w"].data_ptr(),
                                p["enc_b"].data_ptr(), self.h[0].data_ptr(), s)
-        nb = self.ws_block.numel()
         for k, (w, wl, b) in enumerate(p["blocks"]):
+            ws = self.ws_block[k]
             _lib.fno_block_fwd(self.bd, self.prec, self.h[k].data_ptr(), w.data_ptr(),
                                wl.data_ptr(), b.data_ptr(), self.h[k + 1].data_ptr(),
-                               self.ws_block.data_ptr(), nb, s)
+                               ws.data_ptr(), ws.numel(), s)
         _lib.fno_pointwise_fwd(self.dd, self.dec_act, self.h[-1].data_ptr(), p["dec_w"].data_ptr(),
                                p["dec_b"].data_ptr(), self.y.data_ptr(), s)
         return self.y
@@ -181,15 +187,15 @@ class StackRunner:
                                p["dec_b"].data_ptr(), self.dy.data_ptr(), self.g[0].data_ptr(),
                                gr["dec_w"].data_ptr(), gr["dec_b"].data_ptr(),
                                self.ws_pw.data_ptr(), npw, s)
-        nb = self.ws_block.numel()
         cur = 0
         for k in range(self.L - 1, -1, -1):
             w, wl, b = p["blocks"][k]
             dw, dwl, db = gr["blocks"][k]
-            _lib.fno_block_bwd(self.bd, self.prec, self.h[k].data_ptr(), w.data_ptr(),
-                               wl.data_ptr(), b.data_ptr(), self.g[cur].data_ptr(),
-                               self.g[1 - cur].data_ptr(), dw.data_ptr(), dwl.data_ptr(),
-                               db.data_ptr(), self.ws_block.data_ptr(), nb, s)
+            ws = self.ws_block[k]
+            _lib.fno_block_bwd_saved(self.bd, self.prec, self.h[k].data_ptr(), w.data_ptr(),
+                                     wl.data_ptr(), b.data_ptr(), self.g[cur].data_ptr(),
+                                     self.g[1 - cur].data_ptr(), dw.data_ptr(), dwl.data_ptr(),
+                                     db.data_ptr(), ws.data_ptr(), ws.numel(), s)
             cur = 1 - cur
         _lib.fno_pointwise_bwd(self.ed, _lib.FNO_ACT_GELU, x0.data_ptr(), p["enc_w"].data_ptr(),
                                p["enc_b"].data_ptr(), self.g[cur].data_ptr(), None,

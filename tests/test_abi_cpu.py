@@ -138,3 +138,12 @@ def test_pointwise_and_loss_arguments_are_checked_on_the_host():
     assert lib.fno_mse_loss(1000, None, 256, 256, None, 256, nm, None) == -1
     assert lib.fno_mse_loss(1000, 256, 256, None, None, 256, nm, None) == -1
     assert lib.fno_mse_loss(1000, 256, 256, 256, None, 256, nm - 256, None) == -3
+
+
+def test_saved_backward_without_a_recorded_forward_is_refused():
+    lib = _lib.load()
+    d = C1()
+    need = _lib.fno_workspace_bytes(d, 0, _lib.FNO_OP_BLOCK_BWD)
+    rc = lib.fno_block_bwd_saved(ctypes.byref(d), 0, 256, 256, 256, 256, 256, 512, 256, 256, 256,
+                                 1024, need, None)
+    assert rc == -1 and "fno_block_fwd" in _lib.fno_last_error()
