@@ -18,7 +18,8 @@ the t axis keeps kt = 0..mt-1.
 
 The layers around the blocks in Alg. 1 (encoder and decoder pointwise 1x1
 layers with sigma, the mean-squared-error loss) and the composed stack are
-``pointwise_fwd``, ``pointwise_bwd``, ``mse`` and ``stack_loss_and_grads``.
+``pointwise_fwd``, ``pointwise_bwd``, ``mse`` and ``stack_loss_and_grads``; the
+Adam update of a training step is ``adam``.
 
 Parity notes: every routine is pinned by the CPU tests in
 ``tests/test_oracle_pins.py`` (brute-force 4-D sums, NumPy ``rfftn``/``irfftn``,
@@ -127,6 +128,9 @@ def _bind(lib):
     lib.oracle_pointwise_bwd.restype = ci
     lib.oracle_mse.argtypes = [i64, ci, vp, vp, vp, vp]
     lib.oracle_mse.restype = ci
+    dbl = ctypes.c_double
+    lib.oracle_adam.argtypes = [i64, ci, vp, vp, vp, vp, dbl, dbl, dbl, dbl, i64]
+    lib.oracle_adam.restype = ci
     return lib
 
 
@@ -398,3 +402,14 @@ def stack_loss_and_grads(d: Dims, x0, target, enc, blocks, dec, dec_act=1):
     ge = pointwise_bwd(x0, enc[0], dh, enc[1], act=1)
     return loss, {"x0": ge["dx"], "enc": (ge["dw"], ge["db"]), "blocks": gblocks,
                   "dec": (gd["dw"], gd["db"]), "h": h, "y": y}
+
+
+def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (step number t >= 1) on float64 arrays p, m, v (updated in place)."""
+    dt = _dtype_of(g)
+    (g,) = _inputs(dt, g)
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == g.shape
+    _check(_load().oracle_adam(g.size, dt, _ptr(p), _ptr(g), _ptr(m), _ptr(v), float(lr),
+                               float(b1), float(b2), float(eps), int(t)), "adam")
+    return p, m, v

@@ -41,7 +41,8 @@
  * cos/sin calls, for tiny shapes.
  *
  * Around the blocks (Alg. 1): the encoder and decoder pointwise 1x1 layers
- * with sigma, and the mean-squared-error loss, at the end of this file.
+ * with sigma, the mean-squared-error loss, and the Adam update of a training
+ * step, at the end of this file.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,8 +59,9 @@
  * 3 wrong sign of the t exponent, 4 missing 1/N, 5 transposed W_l in the
  * forward, 6 conjugate dropped in dW, 7 GELU' without its second term,
  * 8 bias dropped in the pointwise layer, 9 loss gradient without its factor 2,
- * 10 pointwise sigma' taken at sigma(A) instead of A) and checks that some pin
- * fails.  The oracle itself is built with 0. */
+ * 10 pointwise sigma' taken at sigma(A) instead of A, 11 Adam's second moment
+ * fed g instead of g^2) and checks that some pin fails.  The oracle itself is
+ * built with 0. */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
 #endif
@@ -830,5 +832,30 @@ int oracle_mse(int64_t n, int dtype, const void* y, const void* t, double* loss,
     if (dy) dy[e] = (MUT(9) ? 1.0 : 2.0) * r / (double)n;
   }
   *loss = acc / (double)n;
+  return ORC_OK;
+}
+
+/* ======================================================================== */
+/* Training step: Adam (Kingma and Ba), the optimizer of the original FNO     */
+/* ======================================================================== */
+/*
+ * For step t >= 1 with gradient g:
+ *   m = b1 m + (1 - b1) g;   v = b2 v + (1 - b2) g^2
+ *   p = p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * p, m, v updated in place (FP64); g read as FP32 or FP64 (dtype 0 / 1).
+ */
+int oracle_adam(int64_t n, int dtype, double* p, const void* g, double* m, double* v, double lr,
+                double b1, double b2, double eps, int64_t t) {
+  if (n < 0 || t < 1 || !(b1 >= 0.0 && b1 < 1.0) || !(b2 >= 0.0 && b2 < 1.0) || !(eps > 0.0))
+    return ORC_EINVAL;
+  if (n > 0 && (!p || !g || !m || !v)) return ORC_EINVAL;
+  const double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < n; ++e) {
+    const double gr = ld(g, dtype, e);
+    m[e] = b1 * m[e] + (1.0 - b1) * gr;
+    v[e] = b2 * v[e] + (1.0 - b2) * gr * (MUT(11) ? 1.0 : gr);
+    p[e] -= lr * (m[e] / bc1) / (sqrt(v[e] / bc2) + eps);
+  }
   return ORC_OK;
 }

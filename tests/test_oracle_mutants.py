@@ -6,7 +6,8 @@ one, a dropped c(kt) weight, a wrong sign of the t exponent, a missing 1/N, a
 transposed bypass weight, a conjugate dropped in the weight gradient, a
 GELU derivative missing its second term, a bias dropped in the pointwise
 encoder/decoder layer, a loss gradient missing its factor 2, or the pointwise
-layer's GELU derivative taken at GELU(A) instead of A.  For every mutant at
+layer's GELU derivative taken at GELU(A) instead of A, or Adam's second moment
+fed g instead of g^2.  For every mutant at
 least one pin of tests/test_oracle_pins.py or tests/test_oracle_stack_pins.py
 must fail; the unmutated oracle passes them all.
 """
@@ -29,6 +30,7 @@ PINS = {
     "pointwise grad vs torch": lambda: spins.test_pointwise_gradient_equals_torch_autograd(1),
     "mse vs torch": spins.test_mse_equals_torch_mse_loss_and_its_gradient,
     "stack finite differences": spins.test_stack_gradient_central_finite_differences,
+    "adam vs torch": spins.test_adam_matches_torch_optim_adam,
 }
 
 MUTANTS = {
@@ -42,6 +44,7 @@ MUTANTS = {
     8: "bias dropped in the pointwise layer",
     9: "loss gradient without its factor 2",
     10: "pointwise GELU' taken at GELU(A)",
+    11: "Adam's second moment fed g instead of g^2",
 }
 
 

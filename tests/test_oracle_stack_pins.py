@@ -192,3 +192,29 @@ def test_stack_gradient_central_finite_differences():
     for diff, an in checks:
         fd = diff / (2 * eps)
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * loss), (fd, an)
+
+
+def test_adam_matches_torch_optim_adam():
+    """Three Adam steps against torch.optim.Adam in FP64 (a library routine)."""
+    g = _rng(31)
+    p0 = g.standard_normal(257)
+    grads = [g.standard_normal(257) * s for s in (1.0, 0.3, 2.0)]
+    p, m, v = p0.copy(), np.zeros(257), np.zeros(257)
+    tp = torch.tensor(p0, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=3e-3, betas=(0.85, 0.995), eps=1e-7)
+    for t, gr in enumerate(grads, start=1):
+        oracle.adam(p, gr, m, v, t, lr=3e-3, b1=0.85, b2=0.995, eps=1e-7)
+        opt.zero_grad()
+        tp.grad = torch.from_numpy(gr.copy())
+        opt.step()
+    assert _rel(p - p0, tp.detach().numpy() - p0) < 1e-12
+
+
+def test_adam_first_step_moves_every_coordinate_by_about_lr():
+    """At t = 1 the bias-corrected ratio is g / (|g| + eps): a step of lr against g's sign."""
+    g = _rng(32)
+    p0 = g.standard_normal(100)
+    gr = g.standard_normal(100)
+    p, m, v = p0.copy(), np.zeros(100), np.zeros(100)
+    oracle.adam(p, gr, m, v, 1, lr=0.01, eps=1e-12)
+    np.testing.assert_allclose(p0 - p, 0.01 * np.sign(gr), rtol=1e-9)
