@@ -400,8 +400,9 @@ def run_stack(args, rank, world, local, dev, dist):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    run = (lambda: runner.train_step(x0, tg, lr=1e-4)) if args.train else (lambda: runner.step(x0, tg))
     for _ in range(args.warmup):
-        runner.step(x0, tg)
+        run()
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
@@ -413,7 +414,7 @@ def run_stack(args, rank, world, local, dev, dist):
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        runner.step(x0, tg)
+        run()
     e1.record(stream)
     barrier()
     prof = _lib.fno_profile_stop()
@@ -440,7 +441,7 @@ def run_stack(args, rank, world, local, dev, dist):
         for _ in range(k2):
             x0.copy_(x0_h, non_blocking=True)
             tg.copy_(tg_h, non_blocking=True)
-            runner.step(x0, tg)
+            run()
             for hb, db_ in zip(outs_h, outs):
                 hb.copy_(db_, non_blocking=True)
         e3.record(stream)
@@ -480,8 +481,9 @@ def run_stack(args, rank, world, local, dev, dist):
             "config": {"workload": args.workload, "B": B, "C_in": C0, "width": W, "C_out": Co,
                        "blocks": L, "grid": list(grid), "modes": [mx, my, mz, mt],
                        "precision": args.precision,
-                       "step": "encoder 1x1+GELU, FNO blocks, decoder 1x1+GELU, MSE loss; forward "
-                               "and backward, block inputs kept, spectra recomputed (Alg. 1)",
+                       "step": ("encoder 1x1+GELU, FNO blocks, decoder 1x1+GELU, MSE loss; forward "
+                                "and backward (Alg. 1); block inputs and truncated spectra kept"
+                                + ("; Adam update of every parameter" if args.train else "")),
                        "units": "B*width*N per block, summed over the blocks",
                        "l2": "activations larger than L2; no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -506,6 +508,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--train", action="store_true",
+                    help="stack workloads: each step also takes an Adam update of every parameter")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

@@ -216,6 +216,17 @@ size_t fno_mse_workspace_bytes(int64_t n);
 int fno_mse_loss(int64_t n, const float* y, const float* target, float* loss, float* dy,
                  void* ws, size_t ws_bytes, void* stream);
 
+/* ---- training step -------------------------------------------------------------
+ * One Adam update (Kingma and Ba; the optimizer of the original FNO -- the paper
+ * does not name its own) of n parameters in place, FP32 state, step t >= 1:
+ *   m = beta1 m + (1 - beta1) g;   v = beta2 v + (1 - beta2) g^2
+ *   param -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)
+ * param, m, v read and written, grad read; all device pointers, 4-byte
+ * aligned; m and v start at zero before step 1.  0 <= beta < 1, eps > 0,
+ * lr >= 0.  Asynchronous on stream; no workspace. */
+int fno_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int64_t step, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot hand the library a workspace: for example a host program whose own

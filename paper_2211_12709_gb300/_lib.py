@@ -24,7 +24,7 @@ EXPORTS = (
     "fno_block_bwd", "fno_last_error", "fno_version", "fno_launch_count", "fno_profile_start",
     "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static", "fno_workspace_status", "fno_last_status",
     "fno_pointwise_fwd", "fno_pointwise_workspace_bytes", "fno_pointwise_bwd",
-    "fno_mse_workspace_bytes", "fno_mse_loss", "fno_block_bwd_saved",
+    "fno_mse_workspace_bytes", "fno_mse_loss", "fno_block_bwd_saved", "fno_adam_step",
 )
 FNO_ACT_NONE, FNO_ACT_GELU = 0, 1
 FNO_STATIC_SCRATCH_BYTES = 16 << 20
@@ -103,6 +103,9 @@ def load(build_if_needed: bool = True):
         lib.fno_mse_workspace_bytes.restype = sz
         lib.fno_mse_loss.argtypes = [i64, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_mse_loss.restype = ci
+        fl = ctypes.c_float
+        lib.fno_adam_step.argtypes = [i64, vp, vp, vp, vp, fl, fl, fl, fl, i64, vp]
+        lib.fno_adam_step.restype = ci
         _lib = lib
         return lib
 
@@ -226,3 +229,8 @@ def fno_mse_workspace_bytes(n: int) -> int:
 
 def fno_mse_loss(n, y, target, loss, dy, ws, ws_bytes, stream=0):
     _check(load().fno_mse_loss(int(n), y, target, loss, dy, ws, ws_bytes, stream))
+
+
+def fno_adam_step(n, param, grad, m, v, lr, beta1, beta2, eps, step, stream=0):
+    _check(load().fno_adam_step(int(n), param, grad, m, v, float(lr), float(beta1), float(beta2),
+                                float(eps), int(step), stream))

@@ -10,6 +10,7 @@
 // gives dW and the input-spectrum gradient, and the inverse kernels with the
 // unscaled t table bring it back to the grid.
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -660,6 +661,25 @@ int fno_mse_loss(int64_t n, const float* y, const float* target, float* loss, fl
   if (!ws) return fail(FNO_ERR_WORKSPACE, "workspace is NULL");
   if (!aligned(ws, 256)) return fail(FNO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   CK(launch_mse(y, target, dy, n, loss, static_cast<float*>(ws), (cudaStream_t)stream));
+  return FNO_OK;
+}
+
+int fno_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int64_t step, void* stream) {
+  if (n < 0) return fail(FNO_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+  if (step < 1) return fail(FNO_ERR_INVALID_ARG, "step = %lld must be >= 1", (long long)step);
+  if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f))
+    return fail(FNO_ERR_INVALID_ARG, "beta1 = %g, beta2 = %g must lie in [0, 1)", beta1, beta2);
+  if (!(eps > 0.f) || !(lr >= 0.f))
+    return fail(FNO_ERR_INVALID_ARG, "eps = %g must be > 0 and lr = %g >= 0", eps, lr);
+  if (n == 0) return FNO_OK;
+  REQ(param, 4);
+  REQ(grad, 4);
+  REQ(m, 4);
+  REQ(v, 4);
+  const double bc1 = 1.0 - std::pow((double)beta1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)beta2, (double)step);
+  CK(launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, bc1, bc2, (cudaStream_t)stream));
   return FNO_OK;
 }
 

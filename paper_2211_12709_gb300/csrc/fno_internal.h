@@ -114,6 +114,9 @@ int pointwise_max_grid(int Ci, int Co);  // the most rows launch_pointwise_bwd w
 int mse_max_grid();
 cudaError_t launch_mse(const float* y, const float* t, float* dy, int64_t n, float* loss,
                        float* part, cudaStream_t s);
+// Adam update in place; bc1, bc2 = 1 - beta1^t, 1 - beta2^t
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                        float b1, float b2, float eps, double bc1, double bc2, cudaStream_t s);
 
 // Pruned DFT over t then z with both stages on mma.sync (fno_mma.cu); same
 // contract as launch_fwd_tz_f32.  err: device word set to nonzero when a

@@ -32,6 +32,8 @@
 //
 // Loss: grid-stride pass writing dy with per-thread Kahan sums of (y - t)^2,
 // a fixed-order block reduction to one partial per CTA, and a one-CTA final sum.
+//
+// Training step: an in-place Adam update of one parameter tensor.
 #include <algorithm>
 
 #include "fno_internal.h"
@@ -498,6 +500,46 @@ __global__ void __launch_bounds__(kPwThreads) k_mse_final(const float* __restric
   if (threadIdx.x == 0) *loss = red[0] / (float)n;
 }
 
+// ---------------------------------------------------------------------------
+// training step: Adam (Kingma and Ba), in place, FP32 state
+//   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2
+//   p = p - lr (m / bc1) / (sqrt(v / bc2) + eps),  bc = 1 - beta^t
+// Grid-stride, 16-byte vectors when every pointer allows; 28 bytes per element.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1,
+                                      float b2, float eps, float rbc1, float rbc2) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  p -= lr * (m * rbc1) / (sqrtf(v * rbc2) + eps);
+}
+
+template <int V>
+__global__ void __launch_bounds__(kPwThreads) k_adam(float* __restrict__ p,
+                                                     const float* __restrict__ g,
+                                                     float* __restrict__ m, float* __restrict__ v,
+                                                     long long n, float lr, float b1, float b2,
+                                                     float eps, float rbc1, float rbc2) {
+  const long long nv = n / V;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (V == 4) {
+      float4 pp = reinterpret_cast<float4*>(p)[e];
+      const float4 gg = __ldg(reinterpret_cast<const float4*>(g) + e);
+      float4 mm = reinterpret_cast<float4*>(m)[e];
+      float4 vv = reinterpret_cast<float4*>(v)[e];
+      adam1(pp.x, gg.x, mm.x, vv.x, lr, b1, b2, eps, rbc1, rbc2);
+      adam1(pp.y, gg.y, mm.y, vv.y, lr, b1, b2, eps, rbc1, rbc2);
+      adam1(pp.z, gg.z, mm.z, vv.z, lr, b1, b2, eps, rbc1, rbc2);
+      adam1(pp.w, gg.w, mm.w, vv.w, lr, b1, b2, eps, rbc1, rbc2);
+      reinterpret_cast<float4*>(p)[e] = pp;
+      reinterpret_cast<float4*>(m)[e] = mm;
+      reinterpret_cast<float4*>(v)[e] = vv;
+    } else {
+      adam1(p[e], __ldg(g + e), m[e], v[e], lr, b1, b2, eps, rbc1, rbc2);
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -631,6 +673,28 @@ cudaError_t launch_mse(const float* y, const float* t, float* dy, int64_t n, flo
   else
     FNO_LAUNCH("fno_mse", k_mse<1>, grid, kPwThreads, 0, s, y, t, dy, (long long)n, scale, part);
   FNO_LAUNCH("fno_mse_final", k_mse_final, 1, kPwThreads, 0, s, part, grid, (long long)n, loss);
+  return cudaSuccess;
+}
+
+}  // namespace fno
+
+namespace fno {
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                        float b1, float b2, float eps, double bc1, double bc2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const bool vec = (n % 4 == 0) && ((uintptr_t)p % 16 == 0) && ((uintptr_t)g % 16 == 0) &&
+                   ((uintptr_t)m % 16 == 0) && ((uintptr_t)v % 16 == 0);
+  const long long nv = vec ? n / 4 : n;
+  const int grid = (int)std::max<long long>(
+      1, std::min<long long>((long long)sm_count() * 8, (nv + kPwThreads - 1) / kPwThreads));
+  const float rbc1 = (float)(1.0 / bc1), rbc2 = (float)(1.0 / bc2);
+  if (vec)
+    FNO_LAUNCH("fno_adam", k_adam<4>, grid, kPwThreads, 0, s, p, g, m, v, (long long)n, lr, b1, b2,
+               eps, rbc1, rbc2);
+  else
+    FNO_LAUNCH("fno_adam", k_adam<1>, grid, kPwThreads, 0, s, p, g, m, v, (long long)n, lr, b1, b2,
+               eps, rbc1, rbc2);
   return cudaSuccess;
 }
 

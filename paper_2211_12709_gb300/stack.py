@@ -13,7 +13,8 @@ Two ways to run it, both marshalling only (every step is a libfno kernel):
   only its input for the backward pass, and each block's backward recomputes
   its forward spectrum, so the stack holds one activation per block (per-block
   activation checkpointing).
-* ``StackRunner``: one training pass (forward, loss, backward) issued straight
+* ``StackRunner``: one pass (forward, loss, backward; ``train_step`` adds the
+  Adam update of every parameter, ``fno_adam_step``) issued straight
   through the C ABI with preallocated checkpoints, gradients and workspaces: no
   autograd bookkeeping and no allocation inside the pass, so it can be timed
   or captured as it stands.
@@ -202,3 +203,26 @@ class StackRunner:
                                gr["enc_w"].data_ptr(), gr["enc_b"].data_ptr(),
                                self.ws_pw.data_ptr(), npw, s)
         return self.loss
+
+    # ---- training step ------------------------------------------------------
+    def params_and_grads(self):
+        """(parameter, gradient) pairs in a fixed order."""
+        p, g = self.p, self.grads
+        pairs = [(p["enc_w"], g["enc_w"]), (p["enc_b"], g["enc_b"])]
+        for blk, gb in zip(p["blocks"], g["blocks"]):
+            pairs += list(zip(blk, gb))
+        pairs += [(p["dec_w"], g["dec_w"]), (p["dec_b"], g["dec_b"])]
+        return pairs
+
+    def train_step(self, x0, target, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, stream=None):
+        """step() followed by an Adam update of every parameter (fno_adam_step)."""
+        s = stream if stream is not None else int(torch.cuda.current_stream(self.dev).cuda_stream)
+        loss = self.step(x0, target, s)
+        if not hasattr(self, "_adam"):
+            self._adam = [(torch.zeros_like(q), torch.zeros_like(q)) for q, _ in self.params_and_grads()]
+            self._t = 0
+        self._t += 1
+        for (q, gq), (m, v) in zip(self.params_and_grads(), self._adam):
+            _lib.fno_adam_step(q.numel(), q.data_ptr(), gq.data_ptr(), m.data_ptr(), v.data_ptr(),
+                               lr, betas[0], betas[1], eps, self._t, s)
+        return loss

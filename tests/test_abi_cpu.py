@@ -147,3 +147,14 @@ def test_saved_backward_without_a_recorded_forward_is_refused():
     rc = lib.fno_block_bwd_saved(ctypes.byref(d), 0, 256, 256, 256, 256, 256, 512, 256, 256, 256,
                                  1024, need, None)
     assert rc == -1 and "fno_block_fwd" in _lib.fno_last_error()
+
+
+def test_adam_arguments_are_checked_on_the_host():
+    lib = _lib.load()
+    ok = (256, 256, 256, 256)
+    assert lib.fno_adam_step(16, *ok, 1e-3, 0.9, 0.999, 1e-8, 0, None) == -1   # step 0
+    assert lib.fno_adam_step(16, *ok, 1e-3, 1.0, 0.999, 1e-8, 1, None) == -1   # beta1 = 1
+    assert lib.fno_adam_step(16, *ok, 1e-3, 0.9, 0.999, 0.0, 1, None) == -1    # eps = 0
+    assert lib.fno_adam_step(16, *ok, -1.0, 0.9, 0.999, 1e-8, 1, None) == -1   # lr < 0
+    assert lib.fno_adam_step(16, None, 256, 256, 256, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
+    assert lib.fno_adam_step(0, None, None, None, None, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0

@@ -202,3 +202,48 @@ def test_autograd_module_equals_runner(stack_case):
         assert torch.equal(blk.weight.grad, g[0])
         assert torch.equal(blk.w_lin.grad, g[1])
     assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+
+
+# ---- training step (Adam) ----------------------------------------------------
+@pytest.mark.parametrize("n", [1, 1001, 1 << 20])
+def test_adam_step_matches_oracle(n):
+    from paper_2211_12709_gb300 import _lib
+    g = np.random.Generator(np.random.PCG64(70 + n % 11))
+    p0 = g.standard_normal(n).astype(np.float32)
+    gr = g.standard_normal(n).astype(np.float32)
+    m0 = (0.1 * g.standard_normal(n)).astype(np.float32)
+    v0 = (0.01 * g.random(n)).astype(np.float32)
+    P, G, M, V = (torch.from_numpy(a.copy()).to(DEV) for a in (p0, gr, m0, v0))
+    # a large step (lr 0.1), so that the update is large against one FP32 rounding of p
+    _lib.fno_adam_step(n, P.data_ptr(), G.data_ptr(), M.data_ptr(), V.data_ptr(), 0.1, 0.9, 0.999,
+                       1e-8, 7, int(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    rp, rm, rv = (a.astype(np.float64) for a in (p0, m0, v0))
+    # the oracle takes the hyperparameters the kernel receives (FP32 values)
+    f = lambda c: float(np.float32(c))
+    oracle.adam(rp, gr, rm, rv, 7, lr=f(0.1), b1=f(0.9), b2=f(0.999), eps=f(1e-8))
+    # FP32 state: the update p - p0 within the FP32 bar, 1e-5 rel-L2.  Its error
+    # budget: one FP32 rounding of the stored p (about 6e-7 of an update of size
+    # 0.1 on |p| ~ 1) and a few roundings in the update's arithmetic; where
+    # b1 m and (1 - b1) g nearly cancel, m has a large relative error in any
+    # FP32 implementation, but a small absolute one
+    pg = P.cpu().numpy().astype(np.float64)
+    assert relerr(pg - p0, rp - p0) <= 1e-5
+    assert relerr(M.cpu().numpy(), rm) <= 1e-6
+    assert relerr(V.cpu().numpy(), rv) <= 1e-6
+
+
+def test_training_steps_reduce_the_loss(stack_case):
+    """Forty Adam steps on one synthetic batch: the loss falls well below its start."""
+    from paper_2211_12709_gb300.stack import StackRunner
+    d, x0, target, enc, blocks, dec, ref_loss, ref = stack_case
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+    params = {"enc_w": T(enc[0]), "enc_b": T(enc[1]), "dec_w": T(dec[0]), "dec_b": T(dec[1]),
+              "blocks": [tuple(T(a) for a in blk) for blk in blocks]}
+    r = StackRunner(d.B, C0, d.grid, params, MODES, "bf16x3", device=DEV)
+    X0, TG = T(x0), T(target)
+    losses = [r.train_step(X0, TG, lr=3e-3).item() for _ in range(40)]
+    print("losses", losses[0], losses[9], losses[19], losses[-1])
+    assert abs(losses[0] - ref_loss) <= 1e-5 * ref_loss   # the first loss is the oracle's
+    assert losses[-1] < 0.5 * losses[0]
+    assert sum(b < a for a, b in zip(losses, losses[1:])) >= 30
