@@ -66,9 +66,10 @@ typedef struct fno_dims {
  *   FNO_BF16X3  split BF16 on the tensor cores: hi + lo with three products
  *               in the DFT stages, three-way splits with six products in the
  *               1x1 and line stages
- * The tensor-core precisions need Nz a multiple of 16, Nt a multiple of 8 up
- * to 64, mt <= 8 and 2 mz <= 64 (FNO_ERR_UNSUPPORTED otherwise); stages
- * outside the other tensor-core tilings fall back to the FP32 kernels. */
+ * The tensor-core precisions need Nt even and at most 128, Nz * Nt a multiple
+ * of 4, mt <= 8 and 2 mz <= 64 (FNO_ERR_UNSUPPORTED otherwise); stages outside
+ * the other tensor-core tilings (the fused epilogue takes Nt = 16 or 32) fall
+ * back to the FP32 kernels. */
 typedef enum fno_precision {
   FNO_FP32 = 0,
   FNO_TF32 = 1,

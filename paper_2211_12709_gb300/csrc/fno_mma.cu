@@ -1189,7 +1189,7 @@ namespace {
 
 constexpr int kTzWarps = 8;                      // consumer warps
 constexpr int kTzThreads = 32 * (kTzWarps + 1);
-constexpr int kTzKT = 4;                         // t-stage k-steps (Nt <= 64)
+constexpr int kTzKTMax = 8;                      // t-stage k-steps (Nt <= 128)
 constexpr long long kTzWait = 4000000000LL;      // about 2 s of SM clocks
 
 struct TzM {
@@ -1199,8 +1199,8 @@ struct TzM {
   const float2* Fz;    // [Jz][Nz]  (cos, -sin)
   int* err;
   long long ncol, nunits;   // units: G whole columns, or one column in NCH chunks
-  int Nz, Nt, Jz, Jt, KT, KZ, G, S, NCH, zc;
-  uint32_t col_floats, o_fz, o_ring, stage_bytes, o_bar;
+  int Nz, Nt, Jz, Jt, KT, KZ, G, S, NCH, zc;   // chunks of zc rows (the last may be shorter)
+  uint32_t col_floats, o_fz, o_ft, o_ring, stage_bytes, o_bar;
 };
 
 // Wait (bounded) until the producer has issued stage g; false on timeout or abort.
@@ -1219,7 +1219,9 @@ __device__ __forceinline__ bool tz_wait_issued(volatile int* issued, volatile in
 // need the registers of a whole SM.
 __host__ __device__ constexpr int tz_ctas(int mz) { return mz <= 2 ? 2 : 1; }
 
-template <int MZ, bool SPLIT, bool TF>
+// KTR > 0: the t basis fragments live in registers for up to KTR k-steps (Nt <=
+// 16 KTR); KTR = 0: they are read from a shared-memory table (longer Nt).
+template <int MZ, int KTR, bool SPLIT, bool TF>
 __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __grid_constant__ TzM p) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1241,7 +1243,7 @@ __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __
     const int ln = e & 31, ks = (e >> 5) % p.KZ, mt = (e >> 5) / p.KZ;
     const int r0 = 16 * mt + (ln >> 2), c0 = 16 * ks + 2 * (ln & 3);
     auto F = [&](int kz, int z, int im) -> float {
-      if (kz >= p.Jz) return 0.f;
+      if (kz >= p.Jz || z >= p.Nz) return 0.f;
       const float2 f = p.Fz[(long long)kz * p.Nz + z];
       return rnd<TF>(im ? f.y : f.x);
     };
@@ -1256,6 +1258,25 @@ __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __
       fzf[base] = make_uint4(h[0], h[1], h[2], h[3]);
       fzf[base + 32] = make_uint4(l[0], l[1], l[2], l[3]);
     }
+  }
+  // t basis in A-fragment order: parts (hi, lo); rows ri * 8 + jt, k slots
+  // 2 t4 + {0,1} <-> t = 16 ks + 4 t4 + {0,1} and 2 t4 + 8 + {0,1} <-> + {2,3}
+  uint4* ftf = reinterpret_cast<uint4*>(sm + p.o_ft);  // [KT][2 parts][32 lanes]
+  for (int e = tid; KTR == 0 && e < p.KT * 32; e += kTzThreads) {
+    const int ln = e & 31, ks = e >> 5;
+    const int jt = ln >> 2, t0 = 16 * ks + 4 * (ln & 3);
+    auto F = [&](int ri, int t) -> float {
+      if (jt >= p.Jt || t >= p.Nt) return 0.f;
+      const float2 f = p.Ft[(long long)jt * p.Nt + t];
+      return rnd<TF>(ri ? f.y : f.x);
+    };
+    uint32_t h[4], l[4];
+    split2(F(0, t0), F(0, t0 + 1), h[0], l[0]);
+    split2(F(1, t0), F(1, t0 + 1), h[1], l[1]);
+    split2(F(0, t0 + 2), F(0, t0 + 3), h[2], l[2]);
+    split2(F(1, t0 + 2), F(1, t0 + 3), h[3], l[3]);
+    ftf[(2 * ks) * 32 + ln] = make_uint4(h[0], h[1], h[2], h[3]);
+    ftf[(2 * ks + 1) * 32 + ln] = make_uint4(l[0], l[1], l[2], l[3]);
   }
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -1287,7 +1308,8 @@ __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __
         const int ch = (int)g % p.NCH;
         const long long c0 = u * p.G;
         const long long nc = min((long long)p.G, p.ncol - c0);
-        const uint32_t bytes = (p.NCH > 1) ? (uint32_t)(p.zc * p.Nt * 4)
+        const int rows = min(p.zc, p.Nz - ch * p.zc);  // the last chunk may be shorter
+        const uint32_t bytes = (p.NCH > 1) ? (uint32_t)(rows * p.Nt * 4)
                                            : (uint32_t)(nc * p.col_floats * 4);
         const float* src = p.in + c0 * p.col_floats + (long long)ch * p.zc * p.Nt;
         tma::mbar_arrive_expect_tx(&full[s], bytes);
@@ -1304,22 +1326,26 @@ __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __
 
   // ---------------- consumers ----------------
   const int cw = warp - 1;
-  // t basis A fragments (rows ri * 8 + jt, k slots <-> t = 16 ks + 4 t4 + {0,1} / {2,3})
-  uint32_t fth[kTzKT][4], ftl[kTzKT][4];
+  const int Nt = p.Nt, Nz = p.Nz;
+  // register copy of the t basis fragments (KTR > 0), same layout as the table
+  uint4 frh[KTR > 0 ? KTR : 1], frl[KTR > 0 ? KTR : 1];
 #pragma unroll
-  for (int ks = 0; ks < kTzKT; ++ks) {
+  for (int ks = 0; ks < (KTR > 0 ? KTR : 1); ++ks) {
     const int t0 = 16 * ks + 4 * t4;
     auto F = [&](int ri, int t) -> float {
-      if (g8 >= p.Jt || t >= p.Nt || ks >= p.KT) return 0.f;
-      const float2 f = p.Ft[(long long)g8 * p.Nt + t];
+      if (KTR == 0 || g8 >= p.Jt || t >= Nt || ks >= p.KT) return 0.f;
+      const float2 f = p.Ft[(long long)g8 * Nt + t];
       return rnd<TF>(ri ? f.y : f.x);
     };
-    split2(F(0, t0), F(0, t0 + 1), fth[ks][0], ftl[ks][0]);
-    split2(F(1, t0), F(1, t0 + 1), fth[ks][1], ftl[ks][1]);
-    split2(F(0, t0 + 2), F(0, t0 + 3), fth[ks][2], ftl[ks][2]);
-    split2(F(1, t0 + 2), F(1, t0 + 3), fth[ks][3], ftl[ks][3]);
+    uint32_t h[4], l[4];
+    split2(F(0, t0), F(0, t0 + 1), h[0], l[0]);
+    split2(F(1, t0), F(1, t0 + 1), h[1], l[1]);
+    split2(F(0, t0 + 2), F(0, t0 + 3), h[2], l[2]);
+    split2(F(1, t0 + 2), F(1, t0 + 3), h[3], l[3]);
+    frh[ks] = make_uint4(h[0], h[1], h[2], h[3]);
+    frl[ks] = make_uint4(l[0], l[1], l[2], l[3]);
   }
-  const int Nt = p.Nt;
+  const bool t_vec4 = (Nt & 3) == 0;  // 16-byte rows; otherwise 8-byte (Nt even)
   const int kzc = p.zc / 16;  // z k-steps per staged chunk
   bool ok = true;
   for (int cu = cw; cu < (int)nmine && ok; cu += kTzWarps) {
@@ -1348,30 +1374,47 @@ __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __
         }
         const float* xs = reinterpret_cast<const float*>(sm + p.o_ring + (size_t)s * p.stage_bytes) +
                           (size_t)cl * p.col_floats;
-        for (int kl = 0; kl < kzc; ++kl) {
+        const int kz_end = min(ch * kzc + kzc, p.KZ);
+        for (int kl = 0; ch * kzc + kl < kz_end; ++kl) {
           const int kz = ch * kzc + kl;
-          // t stage of z = 16 kz .. 16 kz + 15 (two n-tiles; staged rows 16 kl ..)
+          // t stage of z = 16 kz .. 16 kz + 15 (two n-tiles; staged rows 16 kl ..);
+          // rows past Nz and times past Nt enter as zeros
           float pc[2][4];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) pc[h][q] = 0.f;
+            const bool zin = 16 * kz + 8 * h + g8 < Nz;
             const float* row = xs + (size_t)(16 * kl + 8 * h + g8) * Nt;
 #pragma unroll
-            for (int ks = 0; ks < kTzKT; ++ks) {
-              if (ks < p.KT) {
-                const int tt = 16 * ks + 4 * t4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (tt < Nt) v = *reinterpret_cast<const float4*>(row + tt);
-                uint32_t bh0, bl0, bh1, bl1;
-                split2(rnd<TF>(v.x), rnd<TF>(v.y), bh0, bl0);
-                split2(rnd<TF>(v.z), rnd<TF>(v.w), bh1, bl1);
-                if (SPLIT) {
-                  mma16(pc[h], ftl[ks][0], ftl[ks][1], ftl[ks][2], ftl[ks][3], bh0, bh1);
-                  mma16(pc[h], fth[ks][0], fth[ks][1], fth[ks][2], fth[ks][3], bl0, bl1);
+            for (int ks = 0; ks < (KTR > 0 ? KTR : kTzKTMax); ++ks) {
+              if (ks >= p.KT) break;
+              const int tt = 16 * ks + 4 * t4;
+              float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (zin && tt < Nt) {
+                if (t_vec4) {
+                  v = *reinterpret_cast<const float4*>(row + tt);
+                } else {
+                  const float2 a = *reinterpret_cast<const float2*>(row + tt);
+                  v.x = a.x;
+                  v.y = a.y;
+                  if (tt + 2 < Nt) {
+                    const float2 b2 = *reinterpret_cast<const float2*>(row + tt + 2);
+                    v.z = b2.x;
+                    v.w = b2.y;
+                  }
                 }
-                mma16(pc[h], fth[ks][0], fth[ks][1], fth[ks][2], fth[ks][3], bh0, bh1);
               }
+              const uint4 fh = KTR > 0 ? frh[KTR > 0 ? ks : 0] : ftf[(2 * ks) * 32 + lane];
+              uint32_t bh0, bl0, bh1, bl1;
+              split2(rnd<TF>(v.x), rnd<TF>(v.y), bh0, bl0);
+              split2(rnd<TF>(v.z), rnd<TF>(v.w), bh1, bl1);
+              if (SPLIT) {
+                const uint4 fl = KTR > 0 ? frl[KTR > 0 ? ks : 0] : ftf[(2 * ks + 1) * 32 + lane];
+                mma16(pc[h], fl.x, fl.y, fl.z, fl.w, bh0, bh1);
+                mma16(pc[h], fh.x, fh.y, fh.z, fh.w, bl0, bl1);
+              }
+              mma16(pc[h], fh.x, fh.y, fh.z, fh.w, bh0, bh1);
             }
           }
           // z stage k-step kz: B fragments straight from the t-stage accumulators
@@ -1440,34 +1483,37 @@ __global__ void __launch_bounds__(kTzThreads, tz_ctas(MZ)) k_fwd_tz_mma(const __
 }  // namespace
 
 // plan: stage columns G (a stage holds at least 8 KB), ring depth S, offsets
+// plan: stages of about 16 KB (G whole columns, or a column in NCH chunks of
+// zc = 16 kzc rows, the last chunk shorter), ring depth S, table offsets
 static bool tz_mma_plan(const Dims& d, TzM& k, size_t& smem) {
   k.Nz = (int)d.Nz;
   k.Nt = (int)d.Nt;
   k.Jz = (int)d.Jz;
   k.Jt = (int)d.Jt;
   k.KT = (int)((d.Nt + 15) / 16);
-  k.KZ = (int)(d.Nz / 16);
+  k.KZ = (int)((d.Nz + 15) / 16);
   const int MZ = (int)((d.Jz + 15) / 16);
   k.col_floats = (uint32_t)(d.Nz * d.Nt);
   const size_t colb = 4 * (size_t)k.col_floats;
   const size_t target = 16 * 1024;  // stage bytes (fewer, larger bulk copies measured faster)
   if (colb > target) {
-    // one column in NCH chunks of zc rows (zc a multiple of 16 dividing Nz)
-    int nch = (int)((colb + target - 1) / target);
-    while (nch < k.KZ && (k.KZ % nch) != 0) ++nch;
-    k.NCH = std::min(nch, k.KZ);
-    k.zc = (int)(d.Nz / k.NCH);
+    const int nch = (int)((colb + target - 1) / target);
+    const int kzc = (k.KZ + nch - 1) / nch;
+    k.NCH = (k.KZ + kzc - 1) / kzc;
+    k.zc = 16 * kzc;
     k.G = 1;
-    k.stage_bytes = (uint32_t)(4 * (size_t)k.zc * d.Nt);
+    k.stage_bytes = (uint32_t)(4 * (size_t)std::min<int64_t>(k.zc, d.Nz) * d.Nt);
   } else {
     k.NCH = 1;
-    k.zc = (int)d.Nz;
+    k.zc = (int)(16 * k.KZ);
     k.G = (int)std::max<size_t>(1, target / colb);
     k.stage_bytes = (uint32_t)(k.G * colb);
   }
   const size_t fzb = (size_t)(MZ <= 1 ? 1 : MZ <= 2 ? 2 : 4) * k.KZ * 4 * 32 * 16;
+  const size_t ftb = k.KT > 4 ? (size_t)k.KT * 2 * 32 * 16 : 0;  // registers up to 4 k-steps
   k.o_fz = 0;
-  k.o_ring = (uint32_t)((fzb + 127) / 128 * 128);
+  k.o_ft = (uint32_t)((fzb + 127) / 128 * 128);
+  k.o_ring = (uint32_t)((k.o_ft + ftb + 127) / 128 * 128);
   const size_t budget = 227 * 1024 / tz_ctas(MZ) - k.o_ring - 1024;
   k.S = (int)std::min<size_t>(32, budget / k.stage_bytes);
   if (k.S < 2) return false;
@@ -1478,10 +1524,10 @@ static bool tz_mma_plan(const Dims& d, TzM& k, size_t& smem) {
 
 bool fwd_tz_mma_supported(const Dims& d, char* why, size_t nwhy) {
   const char* r = nullptr;
-  if (d.Nt % 8 != 0 || d.Nt > 64)
-    r = "the tensor-core t stage needs Nt a multiple of 8 up to 64";
-  else if (d.Nz % 16 != 0)
-    r = "the tensor-core z stage needs Nz a multiple of 16";
+  if (d.Nt % 2 != 0 || d.Nt > 16 * kTzKTMax)
+    r = "the tensor-core t stage needs Nt even and at most 128";
+  else if ((d.Nz * d.Nt) % 4 != 0)
+    r = "the tensor-core t stage needs Nz * Nt a multiple of 4 (16-byte column copies)";
   else if (d.Jt > 8)
     r = "the tensor-core t stage needs mt <= 8";
   else if (d.Jz > 64)
@@ -1495,22 +1541,29 @@ bool fwd_tz_mma_supported(const Dims& d, char* why, size_t nwhy) {
   return r == nullptr;
 }
 
-template <int MZ, bool SPLIT, bool TF>
+template <int MZ, int KTR, bool SPLIT, bool TF>
 static cudaError_t launch_tz_t(const TzM& k, size_t smem, const char* name, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_tz_mma<MZ, SPLIT, TF>,
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_tz_mma<MZ, KTR, SPLIT, TF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid =
       (int)std::max<long long>(1, std::min<long long>((long long)tz_ctas(MZ) * sm_count(), k.nunits));
-  FNO_LAUNCH(name, (k_fwd_tz_mma<MZ, SPLIT, TF>), grid, kTzThreads, smem, s, k);
+  FNO_LAUNCH(name, (k_fwd_tz_mma<MZ, KTR, SPLIT, TF>), grid, kTzThreads, smem, s, k);
   return cudaSuccess;
+}
+
+template <int MZ, int KTR>
+static cudaError_t launch_tz_k(const TzM& k, size_t smem, bool split, bool tf32, cudaStream_t s) {
+  if (tf32) return launch_tz_t<MZ, KTR, true, true>(k, smem, "fno_fwd_tz_mma_tf32", s);
+  if (split) return launch_tz_t<MZ, KTR, true, false>(k, smem, "fno_fwd_tz_mma_bf16x3", s);
+  return launch_tz_t<MZ, KTR, false, false>(k, smem, "fno_fwd_tz_mma_bf16", s);
 }
 
 template <int MZ>
 static cudaError_t launch_tz_m(const TzM& k, size_t smem, bool split, bool tf32, cudaStream_t s) {
-  if (tf32) return launch_tz_t<MZ, true, true>(k, smem, "fno_fwd_tz_mma_tf32", s);
-  if (split) return launch_tz_t<MZ, true, false>(k, smem, "fno_fwd_tz_mma_bf16x3", s);
-  return launch_tz_t<MZ, false, false>(k, smem, "fno_fwd_tz_mma_bf16", s);
+  if (k.KT <= 2) return launch_tz_k<MZ, 2>(k, smem, split, tf32, s);
+  if (k.KT <= 4) return launch_tz_k<MZ, 4>(k, smem, split, tf32, s);
+  return launch_tz_k<MZ, 0>(k, smem, split, tf32, s);
 }
 
 cudaError_t launch_fwd_tz_mma(const float* in, float2* out, int64_t ncol, const Dims& d,

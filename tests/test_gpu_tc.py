@@ -78,6 +78,11 @@ TC_CASES = [
     (Dims(1, 3, 3, 4, 4, 128, 64, 1, 1, 5, 8), "Nz=128, Nt=64: each column in two staged chunks"),
     (Dims(1, 2, 3, 4, 4, 96, 16, 1, 2, 20, 4), "Nz=96, 2mz=40: three z m-tiles"),
     (Dims(2, 2, 2, 4, 4, 32, 24, 1, 1, 4, 6), "Nt=24: the second t k-step half masked"),
+    # non-power-of-two grids like the paper's data (262 x 118 x 64 x 86 and
+    # 130^3 x 84): masked z and t tails, Nt % 4 = 2 (8-byte rows), uneven chunks
+    (Dims(1, 3, 3, 6, 5, 26, 22, 2, 2, 5, 6), "Nz=26, Nt=22: masked z and t tails"),
+    (Dims(1, 2, 3, 4, 3, 64, 86, 1, 1, 6, 8), "Nz=64, Nt=86 (the CO2 data's z, t): two chunks"),
+    (Dims(1, 2, 2, 3, 4, 130, 84, 1, 1, 12, 8), "Nz=130, Nt=84 (the NS data's z, t): chunks 48/48/34"),
 ]
 
 
@@ -136,8 +141,15 @@ def test_tc_full_block_grf_64cube(precision):
 
 def test_tc_unsupported_shapes_are_refused_not_run():
     from paper_2211_12709_gb300 import _lib, ops
-    x = torch.zeros((1, 2, 8, 8, 12, 8), device="cuda")   # Nz=12 is not a tensor-core column height
+    # odd Nt (rows of the staged column would not be 8-byte aligned)
+    x = torch.zeros((1, 2, 8, 8, 12, 7), device="cuda")
     w = torch.zeros((2, 2, 4, 4, 4, 3, 2), device="cuda")
     with pytest.raises(_lib.FnoError) as ei:
         ops.spectral_fwd(x, w, (2, 2, 2, 3), "bf16x3")
+    assert ei.value.status == -2
+    # mt > 8 (the t stage keeps at most 8 kt rows in its m-tile)
+    x = torch.zeros((1, 2, 8, 8, 16, 20), device="cuda")
+    w = torch.zeros((2, 2, 4, 4, 4, 9, 2), device="cuda")
+    with pytest.raises(_lib.FnoError) as ei:
+        ops.spectral_fwd(x, w, (2, 2, 2, 9), "bf16x3")
     assert ei.value.status == -2
