@@ -83,6 +83,9 @@ TC_CASES = [
     (Dims(1, 3, 3, 6, 5, 26, 22, 2, 2, 5, 6), "Nz=26, Nt=22: masked z and t tails"),
     (Dims(1, 2, 3, 4, 3, 64, 86, 1, 1, 6, 8), "Nz=64, Nt=86 (the CO2 data's z, t): two chunks"),
     (Dims(1, 2, 2, 3, 4, 130, 84, 1, 1, 12, 8), "Nz=130, Nt=84 (the NS data's z, t): chunks 48/48/34"),
+    # more channels than the fused tensor-core epilogue takes (32): that stage
+    # runs on the FP32 kernels, the t,z, line and mixing stages stay on theirs
+    (Dims(2, 40, 48, 6, 4, 16, 16, 2, 2, 4, 6), "40 -> 48 channels: FP32 epilogue beside tensor-core stages"),
 ]
 
 
