@@ -176,7 +176,7 @@ TRAFFIC_PER_UNIT = {
     "fno_epi_fwd_mma_bf16x3": (0.801082e9 + 0.633694e9) / 167772160,
     "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
     "fno_epi_dx_mma_bf16x3": (0.800936e9 + 0.616677e9) / 167772160,
-    "fno_fwd_tz_mma_bf16x3": (0.671130e9 + 0.111769e9) / 167772160,
+    "fno_fwd_tz_mma_bf16x3": (0.671163e9 + 0.112208e9) / 167772160,
 }
 
 

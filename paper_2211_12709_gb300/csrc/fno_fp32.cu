@@ -525,19 +525,24 @@ static void epi_layout(const Dims& d, int mode, int Cs, int Cl, size_t off[8], s
   if (mode == EPI_DA) o = al(o + sizeof(float) * (size_t)(Cl * (P + 1)));
   off[6] = o;  // DA: dA tile [CS4][P+1]
   if (mode == EPI_DA) o = al(o + sizeof(float) * (size_t)(CS4 * (P + 1)));
+  // DA: Kahan (sum, compensation) pairs [IB*OB - 128][2][16] of the 4x4 (i, o)
+  // blocks beyond the first 128 (each thread keeps its first block in
+  // registers).  Placed past the first 8 KB, which the final reduction reuses
+  // for the register-held sums.
+  if (mode == EPI_DA) o = std::max(o, (size_t)(128 * 16 * sizeof(float)));
   off[7] = o;
+  if (mode == EPI_DA) {
+    const int nblk = ((Cl + 1 + 3) / 4) * (CS4 / 4);
+    if (nblk > 128) o = al(o + sizeof(float) * 32 * (size_t)(nblk - 128));
+  }
   total = o;
 }
 
 size_t epilogue_smem_bytes(const Dims& d, int mode, int Cs, int Cl) {
   size_t off[8], total;
   epi_layout(d, mode, Cs, Cl, off, total);
-  if (mode == EPI_DA) {
-    // the final reduction reuses the front of shared memory
-    const int IB = (Cl + 1 + 3) / 4, OB = (Cs + 3) / 4;
-    const size_t red = sizeof(float) * 16 * (size_t)(IB * OB) * (size_t)std::max(1, 128 / (IB * OB));
-    total = std::max(total, red);
-  }
+  // in DA mode the final reduction reuses the first 8 KB (128 items x 16
+  // sums), which epi_layout already keeps below the spill region
   return total;
 }
 
@@ -590,11 +595,17 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
     }
   }
 
-  // EPI_DA: this thread's 4x4 block of (i, o) and point group, Kahan running sums
+  // EPI_DA: work items are (4x4 block of (i, o), point group) pairs, item
+  // it = g * nblk + block.  KG point groups split the points when there are
+  // fewer than 128 blocks; with more (KG = 1), a thread owns blocks tid,
+  // tid + 128, ...  Its first item's Kahan running sums live in registers, the
+  // others' in shared memory (racc).
   const int nblk = k.IB * k.OB;
-  const bool wthread = (MODE == EPI_DA) && tid < nblk * k.KG;
-  const int blk = tid % nblk, kg = tid / nblk;
-  const int i0 = (blk / k.OB) * 4, o0w = (blk % k.OB) * 4;
+  const int nitem = nblk * k.KG;
+  const bool wthread = (MODE == EPI_DA) && tid < nitem;
+  float* racc = reinterpret_cast<float*>(base + k.off[7]);
+  if (MODE == EPI_DA)
+    for (int e = tid; e < (nitem - 128) * 32; e += 128) racc[e] = 0.f;
   float wsum[16], wcmp[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -758,29 +769,44 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
       }
       __syncthreads();
       if (wthread) {
-        const int pa = kg * P / k.KG, pb = min((kg + 1) * P / k.KG, valid);
-        float part[16];
+        for (int it = tid; it < nitem; it += 128) {
+          const int bl = it % nblk, kg = it / nblk;
+          const int i0 = (bl / k.OB) * 4, o0w = (bl % k.OB) * 4;
+          const int pa = kg * P / k.KG, pb = min((kg + 1) * P / k.KG, valid);
+          float part[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) part[q] = 0.f;
-        for (int pt = pa; pt < pb; ++pt) {
-          float xv[4], dv[4];
+          for (int q = 0; q < 16; ++q) part[q] = 0.f;
+          for (int pt = pa; pt < pb; ++pt) {
+            float xv[4], dv[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u;
-            xv[u] = i < Cl ? sx[i * PP + pt] : (i == Cl ? 1.f : 0.f);
-            dv[u] = sda[(o0w + u) * PP + pt];
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + u;
+              xv[u] = i < Cl ? sx[i * PP + pt] : (i == Cl ? 1.f : 0.f);
+              dv[u] = sda[(o0w + u) * PP + pt];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) part[u * 4 + v] = fmaf(xv[u], dv[v], part[u * 4 + v]);
           }
+          if (it < 128) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+            for (int q = 0; q < 16; ++q) {
+              const float y = part[q] - wcmp[q];
+              const float s = wsum[q] + y;
+              wcmp[q] = (s - wsum[q]) - y;
+              wsum[q] = s;
+            }
+          } else {
+            float* r = racc + (it - 128) * 32;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) part[u * 4 + v] = fmaf(xv[u], dv[v], part[u * 4 + v]);
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float y = part[q] - wcmp[q];
-          const float s = wsum[q] + y;
-          wcmp[q] = (s - wsum[q]) - y;
-          wsum[q] = s;
+            for (int q = 0; q < 16; ++q) {
+              const float y = part[q] - r[16 + q];
+              const float s = r[q] + y;
+              r[16 + q] = (s - r[q]) - y;
+              r[q] = s;
+            }
+          }
         }
       }
     }
@@ -799,7 +825,10 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
       const int i = (bl / k.OB) * 4 + q / 4, c = (bl % k.OB) * 4 + q % 4;
       float s = 0.f, comp = 0.f;
       for (int g = 0; g < k.KG; ++g) {
-        const float y = red[(g * nblk + bl) * 16 + q] - comp;
+        const int it = g * nblk + bl;
+        const float v = it < 128 ? red[it * 16 + q]
+                                 : racc[(it - 128) * 32 + q] - racc[(it - 128) * 32 + 16 + q];
+        const float y = v - comp;
         const float tt = s + y;
         comp = (tt - s) - y;
         s = tt;

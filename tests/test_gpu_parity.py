@@ -74,6 +74,11 @@ SMALL = [
     (Dims(1, 2, 4, 5, 7, 3, 12, 1, 2, 1, 7), "tiny odd grid, mt = Nt/2+1 with Nyquist"),
     (Dims(2, 17, 9, 20, 8, 40, 8, 5, 3, 7, 2), "tails: 17 channels, Nz=40"),
     (Dims(10, 3, 2, 8, 6, 8, 4, 2, 2, 2, 2), "batch of 10: two batch chunks in the mixing"),
+    # the dW_lin/db reduction works on 4x4 (input + ones row, output) blocks,
+    # one per thread of a 128-thread CTA up to 128 blocks; past that threads
+    # own several: 11 x 12 = 132 blocks, and 17 x 16 = 272 at the 64-channel limit
+    (Dims(2, 40, 48, 6, 4, 16, 16, 2, 2, 4, 6), "40 -> 48 channels: 132 dW_lin blocks"),
+    (Dims(1, 64, 64, 6, 5, 8, 8, 2, 2, 3, 3), "64 -> 64 channels (the limit): 272 dW_lin blocks"),
 ]
 
 

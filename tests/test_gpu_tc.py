@@ -86,6 +86,7 @@ TC_CASES = [
     # more channels than the fused tensor-core epilogue takes (32): that stage
     # runs on the FP32 kernels, the t,z, line and mixing stages stay on theirs
     (Dims(2, 40, 48, 6, 4, 16, 16, 2, 2, 4, 6), "40 -> 48 channels: FP32 epilogue beside tensor-core stages"),
+    (Dims(1, 64, 64, 6, 5, 8, 8, 2, 2, 3, 3), "64 -> 64 channels (the limit), Nz = Nt = 8"),
 ]
 
 
