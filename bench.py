@@ -170,9 +170,9 @@ def algorithmic(name, d):
 # which scales in proportion to the units processed.  An entry is removed when
 # its kernel changes.
 TRAFFIC_PER_UNIT = {
-    "fno_epi_fwd_f32": (0.805e9 + 0.6312e9) / 167772160,
-    "fno_epi_da_f32": (1.476e9 + 0.646e9) / 167772160,
-    "fno_epi_dx_f32": (0.8049e9 + 0.6129e9) / 167772160,
+    "fno_epi_fwd_f32": (0.805050e9 + 0.630492e9) / 167772160,
+    "fno_epi_da_f32": (1.476010e9 + 0.642174e9) / 167772160,
+    "fno_epi_dx_f32": (0.805016e9 + 0.609665e9) / 167772160,
     "fno_epi_fwd_mma_bf16x3": (0.801082e9 + 0.633694e9) / 167772160,
     "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
     "fno_epi_dx_mma_bf16x3": (0.800936e9 + 0.616677e9) / 167772160,

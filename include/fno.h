@@ -51,7 +51,9 @@ extern "C" {
 #endif
 
 /* Problem sizes.  B >= 0 (B = 0 is an empty batch); every other entry >= 1,
- * 2 mx <= Nx, 2 my <= Ny, 2 mz <= Nz, mt <= Nt/2 + 1. */
+ * 2 mx <= Nx, 2 my <= Ny, 2 mz <= Nz, mt <= Nt/2 + 1 (FNO_ERR_INVALID_ARG
+ * otherwise).  Supported: C_in, C_out <= 64 and mt <= 16 (FNO_ERR_UNSUPPORTED
+ * otherwise). */
 typedef struct fno_dims {
   int64_t B, C_in, C_out, Nx, Ny, Nz, Nt, mx, my, mz, mt;
 } fno_dims;

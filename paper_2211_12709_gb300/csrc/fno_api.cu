@@ -98,6 +98,7 @@ int sm_count() {
 
 // ---- validation and workspace layout ---------------------------------------
 static const int64_t kMaxChannels = 64;
+static const int64_t kMaxModesT = 16;
 static const size_t kMaxSmem = 227 * 1024;
 
 static int to_dims(const fno_dims* dd, Dims* d) {
@@ -141,6 +142,9 @@ static int check_support(const Dims& d, int precision, int op) {
   }
   if (d.Ci > kMaxChannels || d.Co > kMaxChannels)
     return fail(FNO_ERR_UNSUPPORTED, "C_in, C_out must be <= %lld", (long long)kMaxChannels);
+  // the inverse t stage of the epilogues keeps its factors in registers
+  if (d.Jt > kMaxModesT)
+    return fail(FNO_ERR_UNSUPPORTED, "mt = %lld must be <= %lld", (long long)d.Jt, (long long)kMaxModesT);
   const size_t need[5] = {
       fwd_tz_smem_bytes(d),
       line_smem_bytes((int)d.Ny, (int)d.Jy),

@@ -470,9 +470,11 @@ cudaError_t launch_mix_adjoint_f32(const Dims& d, const float2* xh, const float2
 
 // ---------------------------------------------------------------------------
 // Inverse z, t stages fused with the pointwise epilogue (FP32 CUDA cores).
-// A 128-thread CTA walks a contiguous range of tiles; a tile is zc z-planes
-// (P = zc * Nt <= 128 points) of one (b, x, y) column and all its channels,
-// one thread per point.
+// A 128-thread CTA walks a contiguous range of tiles; a tile is P = 128
+// consecutive points (z, t) of one (b, x, y) column (fewer at the column's
+// end) and all its channels, one thread per point.  When Nt divides 128 a
+// tile is 128 / Nt whole z-planes; otherwise it starts and ends inside planes
+// and touches at most ZM = 1 + ceil(127 / Nt) of them.
 //   Q[zz][jt][o] = inverse z stage of the column spectrum, with +-k pairing:
 //       Q(z) = sum_{k=0..mz} E_k cos(k th) + i sum_{k=1..mz} O_k sin(k th)
 //       E_0 = U_0, E_k = U_k + U_-k, O_k = U_k - U_-k, E_mz = U_-mz, O_mz = -U_-mz
@@ -484,16 +486,23 @@ cudaError_t launch_mix_adjoint_f32(const Dims& d, const float2* xh, const float2
 struct EpiK {
   EpiArgs a;
   long long NxNy, ntiles;
-  int Nz, Nt, Jz, Jt, mz, zc, P, nzc, CS4;
+  long long nzc;        // tiles per column: ceil(Nz * Nt / 128)
+  int Nz, Nt, Jz, Jt, mz;
+  int ZM;               // z-planes a tile touches at most
+  int P;                // points per tile, min(128, Nz * Nt)
+  int CS4;
   int IB, OB, KG;       // EPI_DA: 4x4 (i, o) blocks of dW_lin, point groups
   int CLW;              // weight rows held in shared memory (the template's channel bound)
   uint32_t off[8];      // shared-memory region offsets (16-byte aligned)
 };
 
-static int epi_zc(const Dims& d) {
-  int zc = (int)std::max<int64_t>(1, 128 / d.Nt);
-  if (zc > d.Nz) zc = (int)d.Nz;
-  return zc;
+constexpr int kEpiP = 128;  // points per tile (one per thread)
+
+// points per tile and the most z-planes a tile touches
+static int epi_points(const Dims& d) { return (int)std::min<int64_t>(kEpiP, d.Nz * d.Nt); }
+static int epi_planes(const Dims& d) {
+  int64_t zm = (kEpiP % d.Nt == 0) ? kEpiP / d.Nt : 1 + (kEpiP - 1 + d.Nt - 1) / d.Nt;
+  return (int)std::min<int64_t>(zm, d.Nz);
 }
 
 // channel bound of the lin-input register array (template CLM) for Cl channels
@@ -506,8 +515,8 @@ static int epi_clm(int Cl) {
 }
 
 static void epi_layout(const Dims& d, int mode, int Cs, int Cl, size_t off[8], size_t& total) {
-  const int zc = epi_zc(d);
-  const int P = zc * (int)d.Nt;
+  const int ZM = epi_planes(d);
+  const int P = epi_points(d);
   const int CS4 = (Cs + 3) / 4 * 4;
   auto al = [](size_t x) { return (x + 15) / 16 * 16; };
   size_t o = 0;
@@ -515,8 +524,8 @@ static void epi_layout(const Dims& d, int mode, int Cs, int Cl, size_t off[8], s
   o = al(o + sizeof(float4) * (size_t)(Cs * d.Jt * (d.mz + 1)));
   off[1] = o;  // cs: [Nz][mz+1] float2
   o = al(o + sizeof(float2) * (size_t)(d.Nz * (d.mz + 1)));
-  off[2] = o;  // qs: [zc][Jt][2][CS4] float
-  o = al(o + sizeof(float) * (size_t)(zc * d.Jt * 2 * CS4));
+  off[2] = o;  // qs: [ZM][Jt][2][CS4] float
+  o = al(o + sizeof(float) * (size_t)(ZM * d.Jt * 2 * CS4));
   off[3] = o;  // w: [CLW][CS4], CLW = Cl rounded up to the kernel's channel bound
   o = al(o + sizeof(float) * (size_t)(epi_clm(Cl) * CS4));
   off[4] = o;  // bias: [CS4]
@@ -553,7 +562,7 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
   extern __shared__ float4 smem4[];
   const EpiArgs& a = k.a;
   const int Cs = a.Cs, Cl = (MODE == EPI_SPECTRAL) ? 0 : a.Cl;
-  const int Jz = k.Jz, Jt = k.Jt, Nz = k.Nz, Nt = k.Nt, mz = k.mz, zc = k.zc, P = k.P, CS4 = k.CS4;
+  const int Jz = k.Jz, Jt = k.Jt, Nz = k.Nz, Nt = k.Nt, mz = k.mz, P = k.P, CS4 = k.CS4;
   const int PP = P + 1;
   unsigned char* base = reinterpret_cast<unsigned char*>(smem4);
   float4* eo = reinterpret_cast<float4*>(base + k.off[0]);
@@ -579,21 +588,11 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
   for (int c = tid; c < CS4; c += 128)
     sbias[c] = ((MODE == EPI_FWD || MODE == EPI_DA) && c < Cs) ? a.bias[c] : 0.f;
 
-  // this thread's point: t is fixed for the whole kernel
+  // this thread's point is p of each tile; its t (and so the inverse-t
+  // factors) changes between tiles only when Nt does not divide 128
   const int p = tid;
-  const int t = p % Nt, zz_p = p / Nt;
+  int cur_t = -1;
   float itr[JTM], iti[JTM];
-#pragma unroll
-  for (int jt = 0; jt < JTM; ++jt) {
-    if (jt < Jt) {
-      const float2 f = a.It[jt * Nt + t];
-      itr[jt] = f.x;
-      iti[jt] = -f.y;
-    } else {
-      itr[jt] = 0.f;
-      iti[jt] = 0.f;
-    }
-  }
 
   // EPI_DA: work items are (4x4 block of (i, o), point group) pairs, item
   // it = g * nblk + block.  KG point groups split the points when there are
@@ -620,10 +619,27 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
   long long cur_col = -1;
   for (long long tau = t_begin; tau < t_end; ++tau) {
     const long long col = tau / k.nzc;
-    const int z0 = (int)(tau - col * k.nzc) * zc;
-    const int zn = min(zc, Nz - z0);
+    const long long s0 = (tau - col * k.nzc) * kEpiP;  // first point of the tile in the column
+    const int valid = (int)min((long long)kEpiP, plane - s0);
+    const int z0 = (int)(s0 / Nt);                      // first plane the tile touches
+    const int tf = (int)(s0 - (long long)z0 * Nt);      // its first point's t
+    const int zn = (tf + valid - 1) / Nt + 1;           // planes touched, <= ZM
     const long long b = col / k.NxNy, xy = col - b * k.NxNy;
-    const int valid = zn * Nt;
+    const int zz_p = (tf + p) / Nt, t = (tf + p) - zz_p * Nt;
+    if (t != cur_t) {
+#pragma unroll
+      for (int jt = 0; jt < JTM; ++jt) {
+        if (jt < Jt) {
+          const float2 f = __ldg(a.It + jt * Nt + t);
+          itr[jt] = f.x;
+          iti[jt] = -f.y;
+        } else {
+          itr[jt] = 0.f;
+          iti[jt] = 0.f;
+        }
+      }
+      cur_t = t;
+    }
     __syncthreads();  // previous tile's shared-memory reads are done
     if (col != cur_col) {
       const int JZT = Jz * Jt;
@@ -656,7 +672,7 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
     }
     // lin inputs of this point (issued early; consumed after Q is ready)
     float x[CLM > 0 ? CLM : 1];
-    const long long pofs = xy * plane + (long long)z0 * Nt + p;
+    const long long pofs = xy * plane + s0 + p;
     const bool pv = p < valid;
     if (MODE != EPI_SPECTRAL) {
       const float* xp = a.lin_in + (b * Cl) * chan + pofs;
@@ -851,9 +867,9 @@ static cudaError_t launch_epi_t(const Dims& d, const EpiArgs& a, int* grid_used,
   k.Jz = (int)d.Jz;
   k.Jt = (int)d.Jt;
   k.mz = (int)d.mz;
-  k.zc = epi_zc(d);
-  k.P = k.zc * (int)d.Nt;
-  k.nzc = (int)((d.Nz + k.zc - 1) / k.zc);
+  k.ZM = epi_planes(d);
+  k.P = epi_points(d);
+  k.nzc = (d.Nz * d.Nt + kEpiP - 1) / kEpiP;
   k.CS4 = (a.Cs + 3) / 4 * 4;
   const int Cl = MODE == EPI_SPECTRAL ? 0 : a.Cl;
   k.IB = (Cl + 1 + 3) / 4;

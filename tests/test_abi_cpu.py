@@ -101,6 +101,16 @@ def test_too_many_channels_is_unsupported_not_a_crash():
     assert "<=" in _lib.fno_last_error()
 
 
+def test_more_than_16_t_modes_is_unsupported_not_wrong():
+    # the epilogues keep the inverse-t factors of at most 16 modes in registers
+    d = C1()
+    d.Nt, d.mt = 40, 17
+    assert raw_ws(d, 0, _lib.FNO_OP_BLOCK_FWD) == 0
+    assert "mt = 17" in _lib.fno_last_error()
+    d.mt = 16
+    assert raw_ws(d, 0, _lib.FNO_OP_BLOCK_FWD) > 0
+
+
 def test_pointwise_and_loss_arguments_are_checked_on_the_host():
     lib = _lib.load()
     d = _lib.make_pw_dims(1, 3, 20, 4096)

@@ -79,6 +79,12 @@ SMALL = [
     # own several: 11 x 12 = 132 blocks, and 17 x 16 = 272 at the 64-channel limit
     (Dims(2, 40, 48, 6, 4, 16, 16, 2, 2, 4, 6), "40 -> 48 channels: 132 dW_lin blocks"),
     (Dims(1, 64, 64, 6, 5, 8, 8, 2, 2, 3, 3), "64 -> 64 channels (the limit): 272 dW_lin blocks"),
+    # the epilogue tiles each (b, x, y) column in runs of 128 points: with Nt
+    # not dividing 128 they start and end inside z-planes, with Nt > 128 a
+    # tile is part of one plane
+    (Dims(2, 3, 4, 4, 3, 20, 22, 2, 1, 5, 6), "Nt=22: tiles start inside z-planes"),
+    (Dims(1, 3, 2, 4, 4, 4, 160, 1, 1, 2, 7), "Nt=160 > 128: a tile is part of a plane"),
+    (Dims(1, 2, 3, 4, 4, 6, 40, 1, 1, 3, 16), "mt=16, the most t modes the epilogue takes"),
 ]
 
 
