@@ -1,9 +1,9 @@
 #!/usr/bin/env python3
 """Benchmark of the 4-D spectral FNO block, forward + backward, on one GB300.
 
-One step = fno_block_fwd + fno_block_bwd_saved (per-block activation
-checkpointing: between the passes only the block input and the forward's
-truncated spectra, kept in the workspace, are held) over one batch of the
+One step = fno_block_fwd_train + fno_block_bwd_saved (per-block activation
+checkpointing: between the passes only the block input, the forward's
+truncated spectra and GELU'(A), kept in the workspace, are held) over one batch of the
 CO2-flow-like block workload: B=1, width 20, grid 128x128x128 (~2.1 M cells)
 x 32 time steps, kept modes 12/12/8/8, input a seeded anisotropic smooth
 Gaussian random field (correlation 20x20x4 cells, 8 steps), upstream gradient
@@ -150,8 +150,10 @@ def algorithmic(name, d):
     f_lin = 2 * B * Ng * Ci * Co
     if name.startswith("fno_fwd_tz"):
         return grid + t1, f_tz
-    if name.startswith("fno_epi_fwd"):
-        return 2 * grid + t1, f_inv + f_lin
+    if name.startswith("fno_epi_fwd"):  # training forward: writes z and GELU'(A)
+        return 3 * grid + t1, f_inv + f_lin
+    if name.startswith("fno_da_saved"):  # reads x, dz, GELU'(A); writes dA
+        return 4 * grid, f_lin
     if name.startswith("fno_epi_da"):
         return 3 * grid + t1, f_inv + 2 * f_lin
     if name.startswith("fno_epi_dx"):
@@ -170,12 +172,12 @@ def algorithmic(name, d):
 # which scales in proportion to the units processed.  An entry is removed when
 # its kernel changes.
 TRAFFIC_PER_UNIT = {
-    "fno_epi_fwd_f32": (0.805050e9 + 0.630492e9) / 167772160,
     "fno_epi_da_f32": (1.476010e9 + 0.642174e9) / 167772160,
     "fno_epi_dx_f32": (0.805016e9 + 0.609665e9) / 167772160,
-    "fno_epi_fwd_mma_bf16x3": (0.801082e9 + 0.633694e9) / 167772160,
     "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
-    "fno_epi_dx_mma_bf16x3": (0.800936e9 + 0.616677e9) / 167772160,
+    "fno_epi_fwd_mma_bf16x3": (0.801008e9 + 1.291166e9) / 167772160,
+    "fno_da_saved": (2.013355e9 + 0.647265e9) / 167772160,
+    "fno_epi_dx_mma_bf16x3": (0.800973e9 + 0.613033e9) / 167772160,
     "fno_fwd_tz_mma_bf16x3": (0.671163e9 + 0.112208e9) / 167772160,
 }
 
@@ -568,19 +570,23 @@ def main():
     d = ops.dims_of(x, C, modes)
     p = ops.precision_code(args.precision)
     nws = max(_lib.fno_workspace_bytes(d, ops.precision_code(q), op)
-              for q in ("fp32", "tf32", "bf16", "bf16x3") for op in (ops.OP_BLOCK_FWD, ops.OP_BLOCK_BWD))
+              for q in ("fp32", "tf32", "bf16", "bf16x3")
+              for op in (ops.OP_BLOCK_FWD, ops.OP_BLOCK_BWD, ops.OP_BLOCK_TRAIN))
     ws = torch.empty(nws, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sh = int(stream.cuda_stream)
 
     def step_of(prec, saved=True):
-        """fno_block_fwd + the backward; saved: reuse the forward's spectra from ws."""
+        """Forward + backward.  saved: fno_block_fwd_train, then the backward reuses
+        the forward's spectra and GELU'(A) from ws; else fno_block_fwd and the
+        backward recomputes them from x."""
         pc = ops.precision_code(prec)
+        fwd = _lib.fno_block_fwd_train if saved else _lib.fno_block_fwd
         bwd = _lib.fno_block_bwd_saved if saved else _lib.fno_block_bwd
 
         def st():
-            _lib.fno_block_fwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
-                               z.data_ptr(), ws.data_ptr(), nws, sh)
+            fwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                z.data_ptr(), ws.data_ptr(), nws, sh)
             bwd(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(), dz.data_ptr(),
                 dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(), db.data_ptr(), ws.data_ptr(), nws, sh)
         return st
@@ -593,8 +599,8 @@ def main():
         xb, dzb, zb, dxb, dwb, dwlb, dbb = bufs
 
         def st():
-            _lib.fno_block_fwd(d, pc, xb.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
-                               zb.data_ptr(), ws.data_ptr(), nws, sh)
+            _lib.fno_block_fwd_train(d, pc, xb.data_ptr(), w.data_ptr(), wl.data_ptr(),
+                                     bias.data_ptr(), zb.data_ptr(), ws.data_ptr(), nws, sh)
             _lib.fno_block_bwd_saved(d, pc, xb.data_ptr(), w.data_ptr(), wl.data_ptr(),
                                      bias.data_ptr(), dzb.data_ptr(), dxb.data_ptr(),
                                      dwb.data_ptr(), dwlb.data_ptr(), dbb.data_ptr(),
@@ -734,8 +740,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "B": B, "C_in": C, "C_out": C,
                        "grid": [Nx, Ny, Nz, Nt], "modes": [mx, my, mz, mt], "precision": args.precision,
-                       "step": "fno_block_fwd + fno_block_bwd_saved (the backward reuses the "
-                               "forward's truncated spectra, kept in the workspace)",
+                       "step": "fno_block_fwd_train + fno_block_bwd_saved (the backward reuses "
+                               "the forward's truncated spectra and GELU'(A), kept in the "
+                               "workspace)",
                        "recompute_ms_per_step": round(ms_rc, 4),
                        "l2": f"inputs larger than L2 ({4 * B * C * Ng / 1e9:.1f} GB per tensor); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -92,7 +92,10 @@ typedef enum fno_op {
   FNO_OP_SPECTRAL_FWD = 0,
   FNO_OP_SPECTRAL_BWD = 1,
   FNO_OP_BLOCK_FWD = 2,
-  FNO_OP_BLOCK_BWD = 3
+  FNO_OP_BLOCK_BWD = 3,
+  /* one workspace for fno_block_fwd_train and the fno_block_bwd_saved after
+   * it: the FNO_OP_BLOCK_BWD layout plus GELU'(A), B * C_out * N floats */
+  FNO_OP_BLOCK_TRAIN = 4
 } fno_op;
 
 /* Workspace bytes that op needs for these sizes and precision (0 on invalid
@@ -119,6 +122,18 @@ int fno_block_fwd(const fno_dims* dims, int precision, const float* x, const flo
                   const float* w_lin, const float* bias, float* z, void* ws, size_t ws_bytes,
                   void* stream);
 
+/* Block forward of a training step: computes z exactly as fno_block_fwd does
+ * and also keeps GELU'(A) at every point in the workspace (B * C_out * N
+ * floats), so that the fno_block_bwd_saved call after it forms dA = dz
+ * GELU'(A) pointwise instead of evaluating the inverse transform and the 1x1
+ * again (the derivative is the one of the erf form of GELU, Sec. IV-C's
+ * block, taken at the forward's own A).  ws_bytes must cover
+ * fno_workspace_bytes(dims, precision, FNO_OP_BLOCK_TRAIN); the workspace is
+ * owned by the caller and must stay untouched until the backward. */
+int fno_block_fwd_train(const fno_dims* dims, int precision, const float* x, const float* w,
+                        const float* w_lin, const float* bias, float* z, void* ws,
+                        size_t ws_bytes, void* stream);
+
 /* Full FNO block backward for upstream gradient dz.  The forward is recomputed
  * from x (activation checkpointing: only the block input is kept between the
  * passes).  dA = dz GELU'(A); db = sum dA; dw_lin = sum x dA^T; dw as in
@@ -132,15 +147,18 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
  * After fno_block_fwd the workspace holds the input's kept spectrum Xh and the
  * inverse x, y partial of the output spectrum (together about 0.35 GB at width
  * 20 on 128^3 x 32, against 5.4 GB for the input); this call takes them from
- * there and runs only the adjoint chain, computing exactly what fno_block_bwd
- * computes.  Per-block checkpointing still holds: only the block input and
- * these truncated spectra live between the passes.
- * Contract: ws (and ws_bytes, sized for FNO_OP_BLOCK_BWD) is the workspace of
- * the last fno_block_fwd call made with it, with the same dims, precision, x
- * and w, and no other call has used ws since; x and w are unchanged.  The
- * library records which forward call left its state in each workspace (host
- * bookkeeping only) and refuses with FNO_ERR_INVALID_ARG when the record does
- * not match; it cannot see writes to x or w made by the caller. */
+ * there and runs only the adjoint chain, computing what fno_block_bwd
+ * computes.  After fno_block_fwd_train it also takes GELU'(A) from there:
+ * dA, dw_lin and db then come from one pointwise pass over x, dz and GELU'(A)
+ * (FP32 products, Kahan-summed), and agree with fno_block_bwd to rounding
+ * rather than bitwise.
+ * Contract: ws (and ws_bytes, sized for FNO_OP_BLOCK_BWD after fno_block_fwd,
+ * FNO_OP_BLOCK_TRAIN after fno_block_fwd_train) is the workspace of the last
+ * forward call made with it, with the same dims, precision, x and w, and no
+ * other call has used ws since; x and w are unchanged.  The library records
+ * which forward call left its state in each workspace (host bookkeeping only)
+ * and refuses with FNO_ERR_INVALID_ARG when the record does not match; it
+ * cannot see writes to x or w made by the caller. */
 int fno_block_bwd_saved(const fno_dims* dims, int precision, const float* x, const float* w,
                         const float* w_lin, const float* bias, const float* dz, float* dx,
                         float* dw, float* dw_lin, float* db, void* ws, size_t ws_bytes,

@@ -14,6 +14,7 @@ from . import _build
 
 FNO_FP32, FNO_TF32, FNO_BF16, FNO_BF16X3 = 0, 1, 2, 3
 FNO_OP_SPECTRAL_FWD, FNO_OP_SPECTRAL_BWD, FNO_OP_BLOCK_FWD, FNO_OP_BLOCK_BWD = 0, 1, 2, 3
+FNO_OP_BLOCK_TRAIN = 4
 FNO_OK = 0
 STATUS_NAMES = {0: "FNO_OK", -1: "FNO_ERR_INVALID_ARG", -2: "FNO_ERR_UNSUPPORTED",
                 -3: "FNO_ERR_WORKSPACE", -4: "FNO_ERR_CUDA", -5: "FNO_ERR_TIMEOUT"}
@@ -25,6 +26,7 @@ EXPORTS = (
     "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static", "fno_workspace_status", "fno_last_status",
     "fno_pointwise_fwd", "fno_pointwise_workspace_bytes", "fno_pointwise_bwd",
     "fno_mse_workspace_bytes", "fno_mse_loss", "fno_block_bwd_saved", "fno_adam_step",
+    "fno_block_fwd_train",
 )
 FNO_ACT_NONE, FNO_ACT_GELU = 0, 1
 FNO_STATIC_SCRATCH_BYTES = 16 << 20
@@ -71,12 +73,13 @@ def load(build_if_needed: bool = True):
         lib.fno_spectral_fwd.argtypes = [dp, ci, vp, vp, vp, vp, sz, vp]
         lib.fno_spectral_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_block_fwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, sz, vp]
+        lib.fno_block_fwd_train.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_spectral_fwd_static.argtypes = [dp, ci, vp, vp, vp, vp]
         lib.fno_spectral_fwd_static.restype = ci
         lib.fno_block_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_block_bwd_saved.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         for f in (lib.fno_spectral_fwd, lib.fno_spectral_bwd, lib.fno_block_fwd, lib.fno_block_bwd,
-                  lib.fno_block_bwd_saved):
+                  lib.fno_block_bwd_saved, lib.fno_block_fwd_train):
             f.restype = ci
         lib.fno_workspace_status.argtypes = [vp, vp]
         lib.fno_workspace_status.restype = ci
@@ -154,6 +157,12 @@ def fno_block_fwd(dims, precision, x, w, w_lin, bias, z, ws, ws_bytes, stream=0)
                                 ws_bytes, stream))
 
 
+def fno_block_fwd_train(dims, precision, x, w, w_lin, bias, z, ws, ws_bytes, stream=0):
+    """fno_block_fwd that also keeps GELU'(A) in ws (sized for FNO_OP_BLOCK_TRAIN)."""
+    _check(load().fno_block_fwd_train(ctypes.byref(dims), int(precision), x, w, w_lin, bias, z,
+                                      ws, ws_bytes, stream))
+
+
 def fno_block_bwd(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws, ws_bytes,
                   stream=0):
     _check(load().fno_block_bwd(ctypes.byref(dims), int(precision), x, w, w_lin, bias, dz, dx, dw,
@@ -162,7 +171,7 @@ def fno_block_bwd(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws
 
 def fno_block_bwd_saved(dims, precision, x, w, w_lin, bias, dz, dx, dw, dw_lin, db, ws, ws_bytes,
                         stream=0):
-    """fno_block_bwd reusing the spectra the last fno_block_fwd left in ws."""
+    """fno_block_bwd reusing the state the last fno_block_fwd(_train) left in ws."""
     _check(load().fno_block_bwd_saved(ctypes.byref(dims), int(precision), x, w, w_lin, bias, dz,
                                       dx, dw, dw_lin, db, ws, ws_bytes, stream))
 

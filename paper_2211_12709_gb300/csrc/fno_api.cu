@@ -134,7 +134,7 @@ static bool is_split(int precision) { return precision == FNO_BF16X3 || precisio
 static int check_support(const Dims& d, int precision, int op) {
   if (precision < FNO_FP32 || precision > FNO_BF16X3)
     return fail(FNO_ERR_INVALID_ARG, "precision %d is not an fno_precision", precision);
-  if (op < FNO_OP_SPECTRAL_FWD || op > FNO_OP_BLOCK_BWD)
+  if (op < FNO_OP_SPECTRAL_FWD || op > FNO_OP_BLOCK_TRAIN)
     return fail(FNO_ERR_INVALID_ARG, "op %d is not an fno_op", op);
   if (is_tc(precision)) {
     char why[256];
@@ -155,9 +155,15 @@ static int check_support(const Dims& d, int precision, int op) {
     if (need[q] > kMaxSmem)
       return fail(FNO_ERR_UNSUPPORTED, "grid/mode sizes need %zu bytes of shared memory in a DFT stage", need[q]);
   const int64_t Cm = d.Ci > d.Co ? d.Ci : d.Co;
-  size_t e = epilogue_smem_bytes(d, op == FNO_OP_BLOCK_BWD ? EPI_DA : EPI_FWD, (int)Cm, (int)Cm);
+  const bool bwd = (op == FNO_OP_BLOCK_BWD || op == FNO_OP_BLOCK_TRAIN);
+  size_t e = epilogue_smem_bytes(d, bwd ? EPI_DA : EPI_FWD, (int)Cm, (int)Cm);
   if (e > kMaxSmem)
     return fail(FNO_ERR_UNSUPPORTED, "channel/grid sizes need %zu bytes of shared memory in the epilogue", e);
+  if (op == FNO_OP_BLOCK_TRAIN) {
+    const size_t p = pointwise_smem_bytes((int)d.Ci, (int)d.Co, true);
+    if (p > kMaxSmem)
+      return fail(FNO_ERR_UNSUPPORTED, "channel counts need %zu bytes of shared memory in the dA pass", p);
+  }
   return FNO_OK;
 }
 
@@ -166,7 +172,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t err;  // device status word (nonzero: a bounded wait gave up)
   size_t tab[10];
-  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, total;
+  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, gp, total;
   bool da_in_dx;
 };
 
@@ -190,11 +196,14 @@ static Layout layout(const Dims& d, int op) {
   off += align256(sizeof(float2) * (size_t)(d.B * d.Ci * d.Mk));
   L.yh = off;
   off += align256(sizeof(float2) * (size_t)(d.B * d.Co * d.Mk));
-  if (op == FNO_OP_SPECTRAL_BWD || op == FNO_OP_BLOCK_BWD) {
+  // the training layout is the backward layout with GELU'(A) appended, so a
+  // workspace sized for it serves both calls of a training step
+  const bool block_bwd = (op == FNO_OP_BLOCK_BWD || op == FNO_OP_BLOCK_TRAIN);
+  if (op == FNO_OP_SPECTRAL_BWD || block_bwd) {
     L.gxh = off;
     off += align256(sizeof(float2) * (size_t)(d.B * d.Ci * d.Mk));
   }
-  if (op == FNO_OP_BLOCK_BWD) {
+  if (block_bwd) {
     // dA lives in dx while dx is not yet written when the channel counts agree
     L.da_in_dx = (d.Ci == d.Co);
     if (!L.da_in_dx) {
@@ -207,6 +216,10 @@ static Layout layout(const Dims& d, int op) {
   }
   L.mma_tab = off;  // basis fragments of the mma.sync epilogue
   off += align256(epilogue_mma_table_bytes(d));
+  if (op == FNO_OP_BLOCK_TRAIN) {
+    L.gp = off;  // GELU'(A) of the training forward, [B][C_out][grid]
+    off += align256(sizeof(float) * (size_t)(d.B * d.Co * d.Ng));
+  }
   L.total = off;
   return L;
 }
@@ -291,7 +304,8 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   const Layout L = layout(d, op);
   if ((rc = check_ws(ws, ws_bytes, L))) return rc;
   REQ(w, 8);
-  if (op == FNO_OP_BLOCK_FWD) {
+  const bool block = (op == FNO_OP_BLOCK_FWD || op == FNO_OP_BLOCK_TRAIN);
+  if (block) {
     REQ(w_lin, 4);
     REQ(bias, 4);
   }
@@ -310,16 +324,17 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   CK(launch_mix_f32(d, xh, reinterpret_cast<const float2*>(w), yh, s));
   if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
   EpiArgs a{};
-  a.mode = (op == FNO_OP_BLOCK_FWD) ? EPI_FWD : EPI_SPECTRAL;
+  a.mode = block ? EPI_FWD : EPI_SPECTRAL;
   a.U = t1;
   a.lin_in = x;
   a.wlin = w_lin;
   a.bias = bias;
   a.out = out;
+  a.gp = (op == FNO_OP_BLOCK_TRAIN) ? reinterpret_cast<float*>(base + L.gp) : nullptr;
   a.Iz = T.Iz;
   a.It = T.Its;
   a.Cs = (int)d.Co;
-  a.Cl = (op == FNO_OP_BLOCK_FWD) ? (int)d.Ci : 0;
+  a.Cl = block ? (int)d.Ci : 0;
   a.w_si = (int)d.Co;
   a.w_sc = 1;
   CK(epilogue(d, a, precision, base, L, err, nullptr, s));
@@ -328,16 +343,18 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
 
 // ---- forward state kept in a workspace ---------------------------------------
 // After fno_block_fwd the workspace holds the block input's kept spectrum X̂ and
-// the inverse x, y partial U1 of the output spectrum; fno_block_bwd_saved
-// reuses them instead of recomputing.  The library remembers, per workspace,
-// which forward call left that state (host-side bookkeeping: no device sync);
-// any other call on the workspace forgets it.
+// the inverse x, y partial U1 of the output spectrum (fno_block_fwd_train adds
+// GELU'(A)); fno_block_bwd_saved reuses them instead of recomputing.  The
+// library remembers, per workspace, which forward call left that state
+// (host-side bookkeeping: no device sync); any other call on the workspace
+// forgets it.
 struct SavedFwd {
   const void* ws;
   const float* x;
   const float* w;
   fno_dims dims;
   int precision;
+  bool train;  // GELU'(A) kept too
 };
 static std::mutex g_saved_mu;
 static std::vector<SavedFwd> g_saved;
@@ -352,19 +369,21 @@ static void saved_forget(const void* ws) {
     }
 }
 static void saved_set(const void* ws, const float* x, const float* w, const fno_dims& dims,
-                      int precision) {
+                      int precision, bool train) {
   saved_forget(ws);
   std::lock_guard<std::mutex> lk(g_saved_mu);
   if (g_saved.size() >= kSavedMax) g_saved.erase(g_saved.begin());
-  g_saved.push_back(SavedFwd{ws, x, w, dims, precision});
+  g_saved.push_back(SavedFwd{ws, x, w, dims, precision, train});
 }
 static bool saved_match(const void* ws, const float* x, const float* w, const fno_dims& dims,
-                        int precision) {
+                        int precision, bool* train) {
   std::lock_guard<std::mutex> lk(g_saved_mu);
   for (const SavedFwd& r : g_saved)
-    if (r.ws == ws)
+    if (r.ws == ws) {
+      *train = r.train;
       return r.x == x && r.w == w && r.precision == precision &&
              std::memcmp(&r.dims, &dims, sizeof(fno_dims)) == 0;
+    }
   return false;
 }
 
@@ -424,7 +443,20 @@ int fno_block_fwd(const fno_dims* dims, int precision, const float* x, const flo
   saved_forget(ws);
   rc = forward_common(d, precision, FNO_OP_BLOCK_FWD, x, w, w_lin, bias, z, ws, ws_bytes,
                       (cudaStream_t)stream);
-  if (rc == FNO_OK && d.B > 0) saved_set(ws, x, w, *dims, precision);
+  if (rc == FNO_OK && d.B > 0) saved_set(ws, x, w, *dims, precision, false);
+  return rc;
+}
+
+int fno_block_fwd_train(const fno_dims* dims, int precision, const float* x, const float* w,
+                        const float* w_lin, const float* bias, float* z, void* ws,
+                        size_t ws_bytes, void* stream) {
+  Dims d;
+  int rc = to_dims(dims, &d);
+  if (rc) return rc;
+  saved_forget(ws);
+  rc = forward_common(d, precision, FNO_OP_BLOCK_TRAIN, x, w, w_lin, bias, z, ws, ws_bytes,
+                      (cudaStream_t)stream);
+  if (rc == FNO_OK && d.B > 0) saved_set(ws, x, w, *dims, precision, true);
   return rc;
 }
 
@@ -518,10 +550,13 @@ static int block_bwd_impl(const fno_dims* dims, int precision, const float* x, c
   const float2* wc = reinterpret_cast<const float2*>(w);
 
   int* err = reinterpret_cast<int*>(base + L.err);
-  if (saved && !saved_match(ws, x, w, *dims, precision))
+  bool train = false;
+  if (saved && !saved_match(ws, x, w, *dims, precision, &train))
     return fail(FNO_ERR_INVALID_ARG,
                 "the workspace does not hold the state of an fno_block_fwd call with these "
                 "dims, precision, x and w");
+  const Layout LT = layout(d, FNO_OP_BLOCK_TRAIN);
+  if (train && (rc = check_ws(ws, ws_bytes, LT))) return rc;
   saved_forget(ws);  // the steps below overwrite the forward state
   CK(launch_tables(d, T, err, s));
   if (!saved) {
@@ -530,6 +565,13 @@ static int block_bwd_impl(const fno_dims* dims, int precision, const float* x, c
     CK(launch_mix_f32(d, xh, wc, yh, s));
     if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
   }
+  int rows = 0;
+  if (train) {
+    // dA = dz GELU'(A) from the training forward's GELU'(A): one pointwise pass
+    // with the partial sums of dW_lin and db
+    CK(launch_pointwise_bwd_saved(x, reinterpret_cast<const float*>(base + LT.gp), dz, da, part,
+                                  epilogue_max_grid(), d.B, d.Ng, (int)d.Ci, (int)d.Co, &rows, s));
+  } else {
   // dA = dz GELU'(A) with the partial sums of dW_lin and db
   EpiArgs a{};
   a.mode = EPI_DA;
@@ -546,8 +588,8 @@ static int block_bwd_impl(const fno_dims* dims, int precision, const float* x, c
   a.Cl = (int)d.Ci;
   a.w_si = (int)d.Co;
   a.w_sc = 1;
-  int rows = 0;
   CK(epilogue(d, a, precision, base, L, err, &rows, s));
+  }
   CK(launch_reduce_partials(part, rows, (int)d.Ci, (int)d.Co, dw_lin, db, s));
   // G = (c/N) DFT(dA); dW and the input-spectrum gradient
   if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s, precision, err))) return rc;

@@ -762,6 +762,7 @@ __global__ void __launch_bounds__(128, 4) k_epi_f32(const EpiK k) {
             float* o = optr + (long long)c * chan;
             if (MODE == EPI_FWD) {
               *o = gelu_f(av[q]);
+              if (a.gp) a.gp[o - a.out] = gelu_grad_f(av[q]);  // training forward
             } else if (MODE == EPI_DA) {
               const float da = dzq[q] * gelu_grad_f(av[q]);
               *o = da;

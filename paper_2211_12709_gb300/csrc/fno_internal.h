@@ -63,6 +63,7 @@ struct EpiArgs {
   const float* bias;    // [Co]
   const float* dz;      // [B][Co][grid] (DA)
   float* out;           // [B][Cs][grid]
+  float* gp;            // FWD, nullable: GELU'(A) [B][Cs][grid] for a training forward
   float* part;          // per-CTA partial sums of dWl and db (DA)
   const float2* Iz;     // [Nz][Jz]
   const float2* It;     // [Jt][Nt]  (Its or Itu)
@@ -108,8 +109,14 @@ cudaError_t launch_pointwise_fwd(const float* x, const float* w, const float* bi
 cudaError_t launch_pointwise_bwd(const float* x, const float* w, const float* bias,
                                  const float* dy, float* dx, float* part, int64_t B, int64_t P,
                                  int Ci, int Co, int act, int* rows_out, cudaStream_t s);
-size_t pointwise_smem_bytes(int Ci, int Co);
+size_t pointwise_smem_bytes(int Ci, int Co, bool saved_grad = false);
 int pointwise_max_grid(int Ci, int Co);  // the most rows launch_pointwise_bwd writes
+// The dA step of a block backward after a training forward: dA = dz * g (g the
+// forward's GELU'(A)), written to da, with the (dW_lin, db) partial sums of
+// x and dA; at most max_rows partial rows (the CTAs launched, *rows_out).
+cudaError_t launch_pointwise_bwd_saved(const float* x, const float* g, const float* dz, float* da,
+                                       float* part, int max_rows, int64_t B, int64_t P, int Ci,
+                                       int Co, int* rows_out, cudaStream_t s);
 // loss = mean((y - t)^2) into *loss, dy = 2 (y - t) / n (nullable); part: mse_max_grid() floats
 int mse_max_grid();
 cudaError_t launch_mse(const float* y, const float* t, float* dy, int64_t n, float* loss,

@@ -726,7 +726,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
     }
     // ---- pointwise epilogue; stores of 8 consecutive points per channel -----
     {
-      float* ob = a.out + (b * Cs + 2 * (lane & 3)) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
+      const long long oofs = (b * Cs + 2 * (lane & 3)) * k.chan + tile_ofs + 16 * warp + (lane >> 2);
+      float* ob = a.out + oofs;
+      // training forward: GELU'(A) beside z, from the same erf evaluation
+      float* gb = (MODE == EPI_FWD && a.gp) ? a.gp + oofs : nullptr;
       const int ob0 = Cs - 2 * (lane & 3);  // channels left for this lane's column pair
       const uint32_t ch = (uint32_t)k.chan;  // 32 * chan < 2^32 (checked on the host)
 #pragma unroll
@@ -734,11 +737,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_epi_mma(const __grid_constant__
         if (nt < NT) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            float v = acc[nt][e];
-            if (MODE == EPI_FWD) v = gelu_as(v);
+            float v = acc[nt][e], g = 0.f;
+            if (MODE == EPI_FWD) {
+              float phi2, ex;
+              phi2_as(v, phi2, ex);
+              g = fmaf(v * ex, 0.39894228040143268f, 0.5f * phi2);  // gelu_grad_as(v)
+              v = 0.5f * v * phi2;                                  // gelu_as(v)
+            }
             if (MODE == EPI_DA) v = dzr[nt][e] * gelu_grad_as(v);
             acc[nt][e] = v;
-            if (8 * nt + (e & 1) < ob0) ob[(uint32_t)(8 * nt + (e & 1)) * ch + 8 * (e >> 1)] = v;
+            if (8 * nt + (e & 1) < ob0) {
+              const uint32_t o = (uint32_t)(8 * nt + (e & 1)) * ch + 8 * (e >> 1);
+              ob[o] = v;
+              if (MODE == EPI_FWD && gb) gb[o] = g;
+            }
           }
         }
       }

@@ -34,6 +34,12 @@
 // a fixed-order block reduction to one partial per CTA, and a one-CTA final sum.
 //
 // Training step: an in-place Adam update of one parameter tensor.
+//
+// The block backward after a training forward uses the same staging for its
+// dA pass: dA = dz GELU'(A) from the forward's saved GELU'(A), written out,
+// with the (dW_lin, db) partial sums.  Up to 31 inputs and 24 outputs that
+// contraction runs on the tensor cores (k_da_mma, split TF32 products);
+// wider layers take the pair blocks of k_pw_bwd.
 #include <algorithm>
 
 #include "fno_internal.h"
@@ -53,6 +59,8 @@ struct PwArgs {
   const float* w;
   const float* bias;  // nullable
   const float* dy;
+  const float* gs;    // nullable: saved act'(A) [B][Co][P] (block backward after a training forward)
+  float* da;          // with gs: dA = dy * gs written here [B][Co][P]
   float* y;           // forward output
   float* dx;          // nullable
   float* part;        // [grid][npair] partial sums of (dw, db)
@@ -237,7 +245,8 @@ struct PwPlan {
   size_t smem;  // bytes
 };
 
-PwPlan pw_plan(int Ci, int Co) {
+// gs: the tiles also stage the saved derivative (C_out more rows)
+PwPlan pw_plan(int Ci, int Co, bool gs = false) {
   PwPlan pl{};
   // blocks of 2 inputs x 4 outputs; 8 inputs x 1 output when C_out = 1
   pl.nbi = (Co == 1) ? (Ci + 8) / 8 : (Ci + 2) / 2;
@@ -246,7 +255,7 @@ PwPlan pw_plan(int Ci, int Co) {
   pl.S = pl.nblk <= kPwThreads ? kPwThreads / pl.nblk : 1;
   pl.KB = (pl.nblk + kPwThreads - 1) / kPwThreads;
   pl.npair = Ci * Co + Co;
-  const size_t stage = sizeof(float) * (size_t)(Ci + 1 + Co) * kPwLd;
+  const size_t stage = sizeof(float) * (size_t)(Ci + 1 + Co + (gs ? Co : 0)) * kPwLd;
   pl.nstage = stage <= kPwTwoStageMax ? 2 : 1;
   const size_t stages = pl.nstage * stage;
   const size_t fold = sizeof(float) * (size_t)pl.S * pl.npair;
@@ -261,13 +270,13 @@ __global__ void __launch_bounds__(kPwThreads, KB == 1 ? 4 : 1) k_pw_bwd(const Pw
   extern __shared__ __align__(16) float sm[];
   const int Ci = k.Ci, Co = k.Co;
   const int npair = Ci * Co + Co;
-  const int RS = Ci + 1 + Co;                          // rows per stage
+  const int RS = Ci + 1 + Co + (k.gs ? Co : 0);       // rows per stage
   float* stage = sm;                                   // [nstage][RS][kPwLd]
   float* fold = sm;                                    // reused at the end: [S][npair]
   float* ws = sm + stage_floats;                       // [Ci][Co]
   float* bs = ws + Ci * Co;                            // [Co]
   const int tid = threadIdx.x;
-  for (int e = tid; e < Ci * Co; e += kPwThreads) ws[e] = k.w[e];
+  for (int e = tid; e < Ci * Co; e += kPwThreads) ws[e] = k.w ? k.w[e] : 0.f;
   for (int e = tid; e < Co; e += kPwThreads) bs[e] = k.bias ? k.bias[e] : 0.f;
 
   // this thread's pair blocks
@@ -286,6 +295,7 @@ __global__ void __launch_bounds__(kPwThreads, KB == 1 ? 4 : 1) k_pw_bwd(const Pw
     float* xs = stage + st * RS * kPwLd;
     stage_rows<VEC>(xs, k.x + q.b * Ci * k.P, Ci, k.P, q.p0, q.np);
     stage_rows<VEC>(xs + (Ci + 1) * kPwLd, k.dy + q.b * Co * k.P, Co, k.P, q.p0, q.np);
+    if (k.gs) stage_rows<VEC>(xs + (Ci + 1 + Co) * kPwLd, k.gs + q.b * Co * k.P, Co, k.P, q.p0, q.np);
     cp_async_commit();
   };
   long long tile = blockIdx.x;
@@ -309,7 +319,16 @@ __global__ void __launch_bounds__(kPwThreads, KB == 1 ? 4 : 1) k_pw_bwd(const Pw
       const bool in = t < np;
       xs[Ci * kPwLd + t] = in ? 1.f : 0.f;
       // dA for this thread's point (its own column only: no barrier needed)
-      if (k.act && in && Co == 1) {  // one output: no channel chunk
+      if (k.gs && in) {  // dA = dy * saved act'(A), kept in the tile and written out
+        const float* gr = ds + Co * kPwLd;
+        float* dout = k.da + (q.b * Co) * k.P + q.p0 + t;
+#pragma unroll 4
+        for (int o = 0; o < Co; ++o) {
+          const float v = ds[o * kPwLd + t] * gr[o * kPwLd + t];
+          ds[o * kPwLd + t] = v;
+          dout[(long long)o * k.P] = v;
+        }
+      } else if (k.act && in && Co == 1) {  // one output: no channel chunk
         float a0 = bs[0];
 #pragma unroll 4
         for (int i = 0; i < Ci; ++i) a0 = fmaf(xs[i * kPwLd + t], ws[i], a0);
@@ -425,6 +444,191 @@ __global__ void __launch_bounds__(kPwThreads, KB == 1 ? 4 : 1) k_pw_bwd(const Pw
       const float yv = fold[r * npair + e] - c;
       const float tv = s + yv;
       c = (tv - s) - yv;
+      s = tv;
+    }
+    k.part[(long long)blockIdx.x * npair + e] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dA pass of a block backward after a training forward, with dW_lin and db on
+// the tensor cores, for C_in + 1 <= 32 rows and C_out <= 24
+// ---------------------------------------------------------------------------
+// A tile is 256 points of one batch entry: rows of x, a row of ones, dz and
+// the saved GELU'(A), staged by cp.async.  Each thread forms dA = dz GELU'(A)
+// for its point in place and writes it out; then warp w contracts points
+// [32 w, 32 w + 32) of the tile:
+//     acc[i][o] += sum_t X[i][t] dA[o][t]      (row i = C_in: the ones row, db)
+// with warp-level mma.sync m16n8k8 on TF32 operands.  Each FP32 operand is
+// split a = big + small (big = a rounded to TF32, small = the rest rounded to
+// TF32) and three products big.big + big.small + small.big are summed, so a
+// product carries about 2^-21 relative error, as FP32 would.  The fragments
+// are read straight from the staged FP32 rows: with the row stride of 260
+// floats the 32 lanes of a fragment load hit 32 different banks.  Per tile the
+// products start from zero (short accumulation chains) and are Kahan-folded
+// into per-thread sums; at the end the CTA adds its warps in a fixed order
+// into one row of partial sums.
+constexpr int kDaMT = 2;  // m-tiles of 16 over the C_in + 1 rows
+constexpr int kDaNT = 3;  // n-tiles of 8 over the C_out columns
+
+__device__ __forceinline__ void tf32_split(float a, uint32_t& big, uint32_t& small) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(big) : "f"(a));
+  const float r = a - __uint_as_float(big);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(small) : "f"(r));
+}
+// D += A (16x8, row) * B (8x8, col), TF32 in, FP32 accumulate
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kPwThreads, 2) k_da_mma(const PwArgs k) {
+  extern __shared__ __align__(16) float sm[];
+  const int Ci = k.Ci, Co = k.Co;
+  const int npair = Ci * Co + Co;
+  const int RS = Ci + 1 + 2 * Co;   // rows per stage: x, ones, dz (then dA), GELU'(A)
+  float* stage = sm;                 // [nstage][RS][kPwLd]
+  float* fold = sm;                  // reused at the end: [8 warps][npair]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, c = lane & 3;
+  const int MT = (Ci + 1 + 15) / 16, NT = (Co + 7) / 8;
+  float sum[kDaMT][kDaNT][4], cmp[kDaMT][kDaNT][4];
+#pragma unroll
+  for (int m = 0; m < kDaMT; ++m)
+#pragma unroll
+    for (int n = 0; n < kDaNT; ++n)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sum[m][n][q] = cmp[m][n][q] = 0.f;
+  // fragment rows of x (clamped to the ones row; the extra rows are discarded)
+  // and of dA (clamped to the last output; discarded likewise)
+  int xr[kDaMT][2], dr[kDaNT];
+#pragma unroll
+  for (int m = 0; m < kDaMT; ++m) {
+    xr[m][0] = min(16 * m + g, Ci) * kPwLd;
+    xr[m][1] = min(16 * m + g + 8, Ci) * kPwLd;
+  }
+#pragma unroll
+  for (int n = 0; n < kDaNT; ++n) dr[n] = min(8 * n + g, Co - 1) * kPwLd;
+
+  const long long tpb = (k.P + kPwTile - 1) / kPwTile;
+  const long long ntiles = k.B * tpb;
+  auto issue = [&](long long tl, int st) {
+    const TileOf q = tile_of(tl, tpb, k.P);
+    float* xs = stage + st * RS * kPwLd;
+    stage_rows<VEC>(xs, k.x + q.b * Ci * k.P, Ci, k.P, q.p0, q.np);
+    stage_rows<VEC>(xs + (Ci + 1) * kPwLd, k.dy + q.b * Co * k.P, Co, k.P, q.p0, q.np);
+    stage_rows<VEC>(xs + (Ci + 1 + Co) * kPwLd, k.gs + q.b * Co * k.P, Co, k.P, q.p0, q.np);
+    cp_async_commit();
+  };
+  long long tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, 0);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const int st = (k.nstage == 2) ? (it & 1) : 0;
+    const long long nxt = tile + gridDim.x;
+    if (k.nstage == 2 && nxt < ntiles) {
+      issue(nxt, st ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // every thread's copies of this tile have landed
+    const TileOf q = tile_of(tile, tpb, k.P);
+    const int np = q.np;
+    float* xs = stage + st * RS * kPwLd;
+    float* ds = xs + (Ci + 1) * kPwLd;
+    {
+      const int t = tid;
+      const bool in = t < np;
+      xs[Ci * kPwLd + t] = in ? 1.f : 0.f;
+      if (in) {  // dA for this thread's point, kept in the tile and written out
+        const float* gr = ds + Co * kPwLd;
+        float* dout = k.da + (q.b * Co) * k.P + q.p0 + t;
+#pragma unroll 4
+        for (int o = 0; o < Co; ++o) {
+          const float v = ds[o * kPwLd + t] * gr[o * kPwLd + t];
+          ds[o * kPwLd + t] = v;
+          dout[(long long)o * k.P] = v;
+        }
+      }
+    }
+    __syncthreads();  // the ones row and dA are in place
+    float acc[kDaMT][kDaNT][4];
+#pragma unroll
+    for (int m = 0; m < kDaMT; ++m)
+#pragma unroll
+      for (int n = 0; n < kDaNT; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[m][n][e] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const int k0 = 32 * warp + 8 * kk;
+      if (k0 >= np) break;  // past the tile's end every operand is zero
+      uint32_t ab[kDaMT][4], as[kDaMT][4];
+#pragma unroll
+      for (int m = 0; m < kDaMT; ++m) {
+        if (m < MT) {
+          tf32_split(xs[xr[m][0] + k0 + c], ab[m][0], as[m][0]);
+          tf32_split(xs[xr[m][1] + k0 + c], ab[m][1], as[m][1]);
+          tf32_split(xs[xr[m][0] + k0 + c + 4], ab[m][2], as[m][2]);
+          tf32_split(xs[xr[m][1] + k0 + c + 4], ab[m][3], as[m][3]);
+        }
+      }
+#pragma unroll
+      for (int n = 0; n < kDaNT; ++n) {
+        if (n < NT) {
+          uint32_t bb0, bs0, bb1, bs1;
+          tf32_split(ds[dr[n] + k0 + c], bb0, bs0);
+          tf32_split(ds[dr[n] + k0 + c + 4], bb1, bs1);
+#pragma unroll
+          for (int m = 0; m < kDaMT; ++m) {
+            if (m < MT) {
+              mma_tf32(acc[m][n], as[m], bb0, bb1);
+              mma_tf32(acc[m][n], ab[m], bs0, bs1);
+              mma_tf32(acc[m][n], ab[m], bb0, bb1);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < kDaMT; ++m)
+#pragma unroll
+      for (int n = 0; n < kDaNT; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {  // Kahan: sum - cmp tracks the exact total
+          const float yv = acc[m][n][e] - cmp[m][n][e];
+          const float tv = sum[m][n][e] + yv;
+          cmp[m][n][e] = (tv - sum[m][n][e]) - yv;
+          sum[m][n][e] = tv;
+        }
+    __syncthreads();  // stage st is free for the copies issued next
+    if (k.nstage == 1 && nxt < ntiles) issue(nxt, 0);
+  }
+  // fold: fold[warp][pair], then a fixed-order sum over the warps per pair
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < kDaMT; ++m)
+#pragma unroll
+    for (int n = 0; n < kDaNT; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 16 * m + g + 8 * (e >> 1), o = 8 * n + 2 * c + (e & 1);
+        if (m < MT && n < NT && i <= Ci && o < Co)
+          fold[warp * npair + (i < Ci ? i * Co + o : Ci * Co + o)] = sum[m][n][e] - cmp[m][n][e];
+      }
+  __syncthreads();
+  for (int e = tid; e < npair; e += kPwThreads) {
+    float s = 0.f, cc = 0.f;
+    for (int w = 0; w < kPwThreads / 32; ++w) {
+      const float yv = fold[w * npair + e] - cc;
+      const float tv = s + yv;
+      cc = (tv - s) - yv;
       s = tv;
     }
     k.part[(long long)blockIdx.x * npair + e] = s;
@@ -567,7 +771,9 @@ static void allow_smem(const void* kern, size_t smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-size_t pointwise_smem_bytes(int Ci, int Co) { return pw_plan(Ci, Co).smem; }
+size_t pointwise_smem_bytes(int Ci, int Co, bool saved_grad) {
+  return pw_plan(Ci, Co, saved_grad).smem;
+}
 
 // The backward's grid, and so the rows of partial sums its workspace holds: the
 // smaller occupancy of its two copy variants, with the shared-memory limit
@@ -656,6 +862,104 @@ cudaError_t launch_pointwise_bwd(const float* x, const float* w, const float* bi
   }
 #undef PW_BWD
   *rows_out = grid;
+  return cudaSuccess;
+}
+
+// tensor-core form of the pass (k_da_mma): staged rows, stages (two when two
+// CTAs per SM still fit), shared-memory bytes
+static bool da_mma_fits(int Ci, int Co) { return Ci + 1 <= 16 * kDaMT && Co <= 8 * kDaNT; }
+static void da_mma_plan(int Ci, int Co, int& nstage, size_t& smem) {
+  const size_t stage = sizeof(float) * (size_t)(Ci + 1 + 2 * Co) * kPwLd;
+  nstage = (2 * stage <= 110 * 1024) ? 2 : 1;
+  smem = std::max(nstage * stage, sizeof(float) * (size_t)(kPwThreads / 32) * (Ci * Co + Co));
+}
+
+static cudaError_t launch_da_mma(const float* x, const float* g, const float* dz, float* da,
+                                 float* part, int max_rows, int64_t B, int64_t P, int Ci, int Co,
+                                 int* rows_out, cudaStream_t s) {
+  int nstage;
+  size_t smem;
+  da_mma_plan(Ci, Co, nstage, smem);
+  PwArgs a{};
+  a.x = x;
+  a.dy = dz;
+  a.gs = g;
+  a.da = da;
+  a.part = part;
+  a.B = B;
+  a.P = P;
+  a.Ci = Ci;
+  a.Co = Co;
+  a.nstage = nstage;
+  const long long ntiles = B * ((P + kPwTile - 1) / kPwTile);
+  const void* kv = reinterpret_cast<const void*>(k_da_mma<true>);
+  const void* ks = reinterpret_cast<const void*>(k_da_mma<false>);
+  allow_smem(kv, smem);
+  allow_smem(ks, smem);
+  const int nb = std::min(pw_blocks_per_sm(kv, smem), pw_blocks_per_sm(ks, smem));
+  long long grid = (long long)sm_count() * std::min(8, nb);
+  grid = std::min<long long>(grid, ntiles);
+  grid = std::min<long long>(grid, max_rows);
+  if (grid < 1) grid = 1;
+  if (rows_aligned(P, x, dz) && rows_aligned(P, g, nullptr))
+    FNO_LAUNCH("fno_da_saved", k_da_mma<true>, (int)grid, kPwThreads, smem, s, a);
+  else
+    FNO_LAUNCH("fno_da_saved", k_da_mma<false>, (int)grid, kPwThreads, smem, s, a);
+  *rows_out = (int)grid;
+  return cudaSuccess;
+}
+
+cudaError_t launch_pointwise_bwd_saved(const float* x, const float* g, const float* dz, float* da,
+                                       float* part, int max_rows, int64_t B, int64_t P, int Ci,
+                                       int Co, int* rows_out, cudaStream_t s) {
+  if (da_mma_fits(Ci, Co))
+    return launch_da_mma(x, g, dz, da, part, max_rows, B, P, Ci, Co, rows_out, s);
+  // wider layers: the FP32 pair-block contraction of k_pw_bwd
+  const PwPlan pl = pw_plan(Ci, Co, true);
+  PwArgs a{};
+  a.x = x;
+  a.dy = dz;
+  a.gs = g;
+  a.da = da;
+  a.part = part;
+  a.B = B;
+  a.P = P;
+  a.Ci = Ci;
+  a.Co = Co;
+  a.act = 0;
+  a.nstage = pl.nstage;
+  const size_t stage_floats =
+      (std::max(pl.nstage * sizeof(float) * (size_t)(Ci + 1 + 2 * Co) * kPwLd,
+                sizeof(float) * (size_t)pl.S * pl.npair) + sizeof(float) - 1) / sizeof(float);
+  const long long ntiles = B * ((P + kPwTile - 1) / kPwTile);
+  const void* kv = pw_bwd_kernel<true>(pl.KB);
+  const void* ks = pw_bwd_kernel<false>(pl.KB);
+  allow_smem(kv, pl.smem);
+  allow_smem(ks, pl.smem);
+  const int nb = std::min(pw_blocks_per_sm(kv, pl.smem), pw_blocks_per_sm(ks, pl.smem));
+  long long grid = (long long)sm_count() * std::min(8, nb);
+  grid = std::min<long long>(grid, ntiles);
+  grid = std::min<long long>(grid, max_rows);
+  if (grid < 1) grid = 1;
+  const bool vec = rows_aligned(P, x, dz) && rows_aligned(P, g, da);
+#define PW_BWD(KB_, V_)                                                                       \
+  FNO_LAUNCH("fno_da_saved", (k_pw_bwd<KB_, V_>), (int)grid, kPwThreads, pl.smem, s, a, pl.nbo, \
+             pl.nblk, pl.S, stage_floats)
+  if (vec) {
+    switch (pl.KB) {
+      case 1: PW_BWD(1, true); break;
+      case 2: PW_BWD(2, true); break;
+      default: PW_BWD(4, true); break;
+    }
+  } else {
+    switch (pl.KB) {
+      case 1: PW_BWD(1, false); break;
+      case 2: PW_BWD(2, false); break;
+      default: PW_BWD(4, false); break;
+    }
+  }
+#undef PW_BWD
+  *rows_out = (int)grid;
   return cudaSuccess;
 }
 

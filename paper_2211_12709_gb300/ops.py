@@ -21,6 +21,7 @@ OP_SPECTRAL_FWD = _lib.FNO_OP_SPECTRAL_FWD
 OP_SPECTRAL_BWD = _lib.FNO_OP_SPECTRAL_BWD
 OP_BLOCK_FWD = _lib.FNO_OP_BLOCK_FWD
 OP_BLOCK_BWD = _lib.FNO_OP_BLOCK_BWD
+OP_BLOCK_TRAIN = _lib.FNO_OP_BLOCK_TRAIN
 
 # When set, every call waits for its stream and raises if a device-side bounded
 # wait gave up (FNO_ERR_TIMEOUT).  For tests and debugging; off by default.
@@ -110,7 +111,9 @@ def spectral_bwd(x, w, dy, modes, need_dx=True, need_dw=True, precision="fp32", 
     return dx, dw
 
 
-def block_fwd(x, w, w_lin, bias, modes, precision="fp32", ws=None):
+def block_fwd(x, w, w_lin, bias, modes, precision="fp32", ws=None, train=False):
+    """Block forward.  train=True also keeps GELU'(A) in ws (sized for
+    OP_BLOCK_TRAIN) for a following block_bwd(..., saved=True)."""
     x = _req(x, "x")
     Ci, Co = x.shape[1], w.shape[1]
     w = _req(w, "w", _wshape(Ci, Co, modes))
@@ -120,16 +123,18 @@ def block_fwd(x, w, w_lin, bias, modes, precision="fp32", ws=None):
     p = precision_code(precision)
     z = torch.empty((x.shape[0], Co) + tuple(x.shape[2:]), dtype=torch.float32, device=x.device)
     if ws is None:
-        ws = workspace(d, p, OP_BLOCK_FWD, x.device)
-    _lib.fno_block_fwd(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(),
-                       z.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(x.device))
+        ws = workspace(d, p, OP_BLOCK_TRAIN if train else OP_BLOCK_FWD, x.device)
+    fn = _lib.fno_block_fwd_train if train else _lib.fno_block_fwd
+    fn(d, p, x.data_ptr(), w.data_ptr(), w_lin.data_ptr(), bias.data_ptr(), z.data_ptr(),
+       ws.data_ptr(), ws.numel(), _stream_handle(x.device))
     _status(ws, x.device)
     return z
 
 
 def block_bwd(x, w, w_lin, bias, dz, modes, precision="fp32", ws=None, saved=False):
-    """Block backward.  saved=True reuses the spectra the last block_fwd left in ws
-    (the workspace of that call, sized for OP_BLOCK_BWD) instead of recomputing them."""
+    """Block backward.  saved=True reuses the state the last block_fwd left in ws
+    (the workspace of that call, sized for OP_BLOCK_BWD, or OP_BLOCK_TRAIN after a
+    training forward) instead of recomputing it."""
     x = _req(x, "x")
     Ci, Co = x.shape[1], w.shape[1]
     w = _req(w, "w", _wshape(Ci, Co, modes))
@@ -178,8 +183,9 @@ class FNOBlock4dFn(torch.autograd.Function):
 
     Between the passes the block keeps its input and the forward's workspace,
     which holds the truncated spectra (X̂ and the inverse x, y partial U1, a
-    small fraction of x); the backward reuses them.  A second backward through
-    the same graph finds the workspace spent and recomputes the spectra.
+    small fraction of x) and GELU'(A) (one output-sized tensor); the backward
+    reuses them.  A second backward through the same graph finds the workspace
+    spent and recomputes the spectra.
     """
 
     @staticmethod
@@ -189,8 +195,8 @@ class FNOBlock4dFn(torch.autograd.Function):
         ctx.save_for_backward(x, w, w_lin, bias)
         x = _req(x, "x")
         d = dims_of(x, int(w.shape[1]), ctx.modes)
-        ctx.ws = workspace(d, precision, OP_BLOCK_BWD, x.device)
-        return block_fwd(x, w, w_lin, bias, ctx.modes, precision, ws=ctx.ws)
+        ctx.ws = workspace(d, precision, OP_BLOCK_TRAIN, x.device)
+        return block_fwd(x, w, w_lin, bias, ctx.modes, precision, ws=ctx.ws, train=True)
 
     @staticmethod
     def backward(ctx, dz):

@@ -132,9 +132,9 @@ class StackRunner:
         }
         mx, my, mz, mt = self.modes
         self.bd = _lib.make_dims(self.B, W, W, *self.grid, mx, my, mz, mt)
-        nb = max(_lib.fno_workspace_bytes(self.bd, self.prec, ops.OP_BLOCK_FWD),
-                 _lib.fno_workspace_bytes(self.bd, self.prec, ops.OP_BLOCK_BWD))
-        # one workspace per block: it carries the block's truncated spectra from
+        nb = _lib.fno_workspace_bytes(self.bd, self.prec, ops.OP_BLOCK_TRAIN)
+        # one workspace per block (the training size covers the forward and the
+        # backward): it carries the block's truncated spectra and GELU'(A) from
         # the forward to the backward (fno_block_bwd_saved)
         self.ws_block = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(self.L)]
         self.ed = _lib.make_pw_dims(self.B, self.c_in, W, self.P)
@@ -158,8 +158,9 @@ class StackRunner:
             if not target.is_contiguous():
                 raise ValueError("target must be contiguous")
 
-    def forward(self, x0, stream=None):
-        """Y for input x0 [B, C_in, *grid]; fills the block-input checkpoints."""
+    def forward(self, x0, stream=None, train=False):
+        """Y for input x0 [B, C_in, *grid]; fills the block-input checkpoints
+        (train=True: the blocks also keep GELU'(A) for the backward)."""
         self._check_io(x0)
         s = stream if stream is not None else int(torch.cuda.current_stream(self.dev).cuda_stream)
         p = self.p
@@ -167,9 +168,9 @@ class StackRunner:
                                p["enc_b"].data_ptr(), self.h[0].data_ptr(), s)
         for k, (w, wl, b) in enumerate(p["blocks"]):
             ws = self.ws_block[k]
-            _lib.fno_block_fwd(self.bd, self.prec, self.h[k].data_ptr(), w.data_ptr(),
-                               wl.data_ptr(), b.data_ptr(), self.h[k + 1].data_ptr(),
-                               ws.data_ptr(), ws.numel(), s)
+            fwd = _lib.fno_block_fwd_train if train else _lib.fno_block_fwd
+            fwd(self.bd, self.prec, self.h[k].data_ptr(), w.data_ptr(), wl.data_ptr(),
+                b.data_ptr(), self.h[k + 1].data_ptr(), ws.data_ptr(), ws.numel(), s)
         _lib.fno_pointwise_fwd(self.dd, self.dec_act, self.h[-1].data_ptr(), p["dec_w"].data_ptr(),
                                p["dec_b"].data_ptr(), self.y.data_ptr(), s)
         return self.y
@@ -179,7 +180,7 @@ class StackRunner:
         self._check_io(x0, target)
         s = stream if stream is not None else int(torch.cuda.current_stream(self.dev).cuda_stream)
         p, gr = self.p, self.grads
-        self.forward(x0, s)
+        self.forward(x0, s, train=True)
         n = self.y.numel()
         _lib.fno_mse_loss(n, self.y.data_ptr(), target.data_ptr(), self.loss.data_ptr(),
                           self.dy.data_ptr(), self.ws_mse.data_ptr(), self.ws_mse.numel(), s)

@@ -101,6 +101,19 @@ def test_too_many_channels_is_unsupported_not_a_crash():
     assert "<=" in _lib.fno_last_error()
 
 
+def test_training_workspace_is_the_backward_one_plus_gelu_derivative():
+    d = C1()
+    bwd = _lib.fno_workspace_bytes(d, 0, _lib.FNO_OP_BLOCK_BWD)
+    train = _lib.fno_workspace_bytes(d, 0, _lib.FNO_OP_BLOCK_TRAIN)
+    n = d.B * d.C_out * d.Nx * d.Ny * d.Nz * d.Nt
+    assert train == bwd + (4 * n + 255) // 256 * 256
+    lib = _lib.load()
+    # a backward-sized workspace is refused before any pointer is touched
+    rc = lib.fno_block_fwd_train(ctypes.byref(d), 0, 256, 256, 256, 256, 256, 256, bwd, None)
+    assert rc == -3 and str(train) in _lib.fno_last_error()
+    assert raw_ws(d, 0, 5) == 0  # no op 5
+
+
 def test_more_than_16_t_modes_is_unsupported_not_wrong():
     # the epilogues keep the inverse-t factors of at most 16 modes in registers
     d = C1()

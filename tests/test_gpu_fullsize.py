@@ -3,8 +3,9 @@
 The CO2-like block: B = 1, width 20, grid 128 x 128 x 128 x 32 (2.1 M cells x
 32 steps), kept modes 12/12/8/8, input the same seeded anisotropic Gaussian
 random field that bench.py times (correlation 20 x 20 x 4 cells, 8 steps),
-upstream gradient N(0, 1).  The GPU runs fno_block_fwd + fno_block_bwd through
-the C ABI with one workspace, as the benchmark does.  The FP64 oracle computes
+upstream gradient N(0, 1).  The GPU runs, through the C ABI with one workspace,
+fno_block_fwd_train + fno_block_bwd_saved (the step the benchmark times) and
+fno_block_fwd + fno_block_bwd (the recompute form).  The FP64 oracle computes
 the full kept spectra (Alg. 2) and evaluates Z and dX at 96 sampled grid points
 (corners and edges of every axis included); dW, dW_lin and db are compared in
 full.  Tolerance: rel-L2 per tensor, FP32 and split BF16 <= 1e-5, BF16 <= 2e-2,
@@ -61,8 +62,9 @@ def case():
     return d, x, w, wl, b, dz, pts, ref
 
 
+@pytest.mark.parametrize("path", ["train+saved", "recompute"])
 @pytest.mark.parametrize("precision", ["bf16x3", "fp32", "bf16", "tf32"])
-def test_block_fwd_bwd_full_size_sampled(case, precision):
+def test_block_fwd_bwd_full_size_sampled(case, precision, path):
     from paper_2211_12709_gb300 import _lib, ops
     d, x, w, wl, b, dz, pts, ref = case
     dev = torch.device("cuda", 0)
@@ -78,15 +80,16 @@ def test_block_fwd_bwd_full_size_sampled(case, precision):
     DB = torch.empty_like(Bb)
     dims = ops.dims_of(X, d.Co, (d.mx, d.my, d.mz, d.mt))
     p = ops.precision_code(precision)
-    nws = max(_lib.fno_workspace_bytes(dims, p, ops.OP_BLOCK_FWD),
-              _lib.fno_workspace_bytes(dims, p, ops.OP_BLOCK_BWD))
+    train = path == "train+saved"
+    nws = _lib.fno_workspace_bytes(dims, p, ops.OP_BLOCK_TRAIN if train else ops.OP_BLOCK_BWD)
     ws = torch.empty(nws, dtype=torch.uint8, device=dev)
     sh = int(torch.cuda.current_stream(dev).cuda_stream)
-    _lib.fno_block_fwd(dims, p, X.data_ptr(), W.data_ptr(), WL.data_ptr(), Bb.data_ptr(),
-                       Z.data_ptr(), ws.data_ptr(), nws, sh)
-    _lib.fno_block_bwd(dims, p, X.data_ptr(), W.data_ptr(), WL.data_ptr(), Bb.data_ptr(),
-                       DZ.data_ptr(), DX.data_ptr(), DW.data_ptr(), DWL.data_ptr(), DB.data_ptr(),
-                       ws.data_ptr(), nws, sh)
+    fwd = _lib.fno_block_fwd_train if train else _lib.fno_block_fwd
+    bwd = _lib.fno_block_bwd_saved if train else _lib.fno_block_bwd
+    fwd(dims, p, X.data_ptr(), W.data_ptr(), WL.data_ptr(), Bb.data_ptr(), Z.data_ptr(),
+        ws.data_ptr(), nws, sh)
+    bwd(dims, p, X.data_ptr(), W.data_ptr(), WL.data_ptr(), Bb.data_ptr(), DZ.data_ptr(),
+        DX.data_ptr(), DW.data_ptr(), DWL.data_ptr(), DB.data_ptr(), ws.data_ptr(), nws, sh)
     _lib.fno_workspace_status(ws.data_ptr(), sh)
     torch.cuda.synchronize()
     ix = [torch.from_numpy(pts[:, a]).to(dev) for a in range(4)]
@@ -95,5 +98,5 @@ def test_block_fwd_bwd_full_size_sampled(case, precision):
     errs = {"z": relerr(z_pts, ref["z_pts"]), "dx": relerr(dx_pts, ref["dx_pts"]),
             "dw": relerr(DW.cpu().numpy(), ref["dw"]), "dwl": relerr(DWL.cpu().numpy(), ref["dwl"]),
             "db": relerr(DB.cpu().numpy(), ref["db"])}
-    print("128^3x32 width 20", precision, errs)
+    print("128^3x32 width 20", precision, path, errs)
     assert all(np.isfinite(v) and v <= TOL[precision] for v in errs.values()), errs
