@@ -150,8 +150,10 @@ def algorithmic(name, d):
     f_lin = 2 * B * Ng * Ci * Co
     if name.startswith("fno_fwd_tz"):
         return grid + t1, f_tz
-    if name.startswith("fno_epi_fwd"):  # training forward: writes z and GELU'(A)
+    if name.startswith("fno_epi_fwd_train"):  # training forward: writes z and GELU'(A)
         return 3 * grid + t1, f_inv + f_lin
+    if name.startswith("fno_epi_fwd"):
+        return 2 * grid + t1, f_inv + f_lin
     if name.startswith("fno_da_saved"):  # reads x, dz, GELU'(A); writes dA
         return 4 * grid, f_lin
     if name.startswith("fno_epi_da"):
@@ -172,10 +174,11 @@ def algorithmic(name, d):
 # which scales in proportion to the units processed.  An entry is removed when
 # its kernel changes.
 TRAFFIC_PER_UNIT = {
+    "fno_epi_fwd_train_f32": (0.804905e9 + 1.289400e9) / 167772160,
     "fno_epi_da_f32": (1.476010e9 + 0.642174e9) / 167772160,
-    "fno_epi_dx_f32": (0.805016e9 + 0.609665e9) / 167772160,
+    "fno_epi_dx_f32": (0.804837e9 + 0.609467e9) / 167772160,
     "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
-    "fno_epi_fwd_mma_bf16x3": (0.801008e9 + 1.291166e9) / 167772160,
+    "fno_epi_fwd_train_mma_bf16x3": (0.801008e9 + 1.291166e9) / 167772160,
     "fno_da_saved": (2.013355e9 + 0.647265e9) / 167772160,
     "fno_epi_dx_mma_bf16x3": (0.800973e9 + 0.613033e9) / 167772160,
     "fno_fwd_tz_mma_bf16x3": (0.671163e9 + 0.112208e9) / 167772160,

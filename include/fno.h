@@ -127,9 +127,13 @@ int fno_block_fwd(const fno_dims* dims, int precision, const float* x, const flo
  * floats), so that the fno_block_bwd_saved call after it forms dA = dz
  * GELU'(A) pointwise instead of evaluating the inverse transform and the 1x1
  * again (the derivative is the one of the erf form of GELU, Sec. IV-C's
- * block, taken at the forward's own A).  ws_bytes must cover
- * fno_workspace_bytes(dims, precision, FNO_OP_BLOCK_TRAIN); the workspace is
- * owned by the caller and must stay untouched until the backward. */
+ * block, taken at the forward's own A).  In the tensor-core precisions with
+ * more than 31 input or 24 output channels (up to 32) re-evaluating A on the
+ * tensor cores is the faster form: there the call skips the store and the
+ * saved backward re-evaluates A, as after fno_block_fwd.  ws_bytes must cover
+ * fno_workspace_bytes(dims, precision, FNO_OP_BLOCK_TRAIN) in every case; the
+ * workspace is owned by the caller and must stay untouched until the
+ * backward. */
 int fno_block_fwd_train(const fno_dims* dims, int precision, const float* x, const float* w,
                         const float* w_lin, const float* bias, float* z, void* ws,
                         size_t ws_bytes, void* stream);

@@ -296,6 +296,17 @@ static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base,
   return launch_epilogue_f32(d, a, grid_used, s);
 }
 
+// Whether a training forward keeps GELU'(A) for the backward's dA pass.  The
+// pass wins wherever it contracts dW_lin on the tensor cores, and over the FP32
+// dA epilogue; with more channels than that in the tensor-core precisions, the
+// tensor-core dA epilogue (A re-evaluated from the kept spectra) is the faster
+// form, and the forward skips the store.
+static bool keep_gelu_grad(const Dims& d, int precision) {
+  if (pointwise_da_mma_fits((int)d.Ci, (int)d.Co)) return true;
+  return !(is_tc(precision) &&
+           epilogue_mma_supported(d, EPI_DA, (int)d.Co, (int)d.Ci, nullptr, 0));
+}
+
 static int forward_common(const Dims& d, int precision, int op, const float* x, const float* w,
                           const float* w_lin, const float* bias, float* out, void* ws,
                           size_t ws_bytes, cudaStream_t s) {
@@ -330,7 +341,9 @@ static int forward_common(const Dims& d, int precision, int op, const float* x, 
   a.wlin = w_lin;
   a.bias = bias;
   a.out = out;
-  a.gp = (op == FNO_OP_BLOCK_TRAIN) ? reinterpret_cast<float*>(base + L.gp) : nullptr;
+  a.gp = (op == FNO_OP_BLOCK_TRAIN && keep_gelu_grad(d, precision))
+             ? reinterpret_cast<float*>(base + L.gp)
+             : nullptr;
   a.Iz = T.Iz;
   a.It = T.Its;
   a.Cs = (int)d.Co;
@@ -456,7 +469,7 @@ int fno_block_fwd_train(const fno_dims* dims, int precision, const float* x, con
   saved_forget(ws);
   rc = forward_common(d, precision, FNO_OP_BLOCK_TRAIN, x, w, w_lin, bias, z, ws, ws_bytes,
                       (cudaStream_t)stream);
-  if (rc == FNO_OK && d.B > 0) saved_set(ws, x, w, *dims, precision, true);
+  if (rc == FNO_OK && d.B > 0) saved_set(ws, x, w, *dims, precision, keep_gelu_grad(d, precision));
   return rc;
 }
 

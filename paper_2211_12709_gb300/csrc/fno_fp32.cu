@@ -892,7 +892,9 @@ static cudaError_t launch_epi_t(const Dims& d, const EpiArgs& a, int* grid_used,
   if (grid_used) *grid_used = grid;
   static const char* names[4] = {"fno_epi_spectral_f32", "fno_epi_fwd_f32", "fno_epi_da_f32",
                                  "fno_epi_dx_f32"};
-  FNO_LAUNCH(names[MODE], (k_epi_f32<MODE, CLM, JTM>), grid, 128, smem, s, k);
+  // the forward of a training step also stores GELU'(A)
+  const char* name = (MODE == EPI_FWD && a.gp) ? "fno_epi_fwd_train_f32" : names[MODE];
+  FNO_LAUNCH(name, (k_epi_f32<MODE, CLM, JTM>), grid, 128, smem, s, k);
   return cudaSuccess;
 }
 

@@ -114,6 +114,8 @@ int pointwise_max_grid(int Ci, int Co);  // the most rows launch_pointwise_bwd w
 // The dA step of a block backward after a training forward: dA = dz * g (g the
 // forward's GELU'(A)), written to da, with the (dW_lin, db) partial sums of
 // x and dA; at most max_rows partial rows (the CTAs launched, *rows_out).
+// the dA pass contracts dW_lin on the tensor cores (else on the CUDA cores)
+bool pointwise_da_mma_fits(int Ci, int Co);
 cudaError_t launch_pointwise_bwd_saved(const float* x, const float* g, const float* dz, float* da,
                                        float* part, int max_rows, int64_t B, int64_t P, int Ci,
                                        int Co, int* rows_out, cudaStream_t s);

@@ -868,7 +868,13 @@ static cudaError_t launch_mma_t(const EpiM& k, int* grid_used, cudaStream_t s) {
       {"fno_epi_spectral_mma_bf16x3", "fno_epi_fwd_mma_bf16x3", "fno_epi_da_mma_bf16x3",
        "fno_epi_dx_mma_bf16x3"},
       {"fno_epi_spectral_mma_tf32", "fno_epi_fwd_mma_tf32", "fno_epi_da_mma_tf32", "fno_epi_dx_mma_tf32"}};
-  FNO_LAUNCH(names[TF ? 2 : (SPLIT ? 1 : 0)][MODE], (k_epi_mma<MODE, SPLIT, TF>), (int)g, kThreads, smem, s, k);
+  // the forward of a training step also stores GELU'(A): its own name, so that
+  // timings and byte counts tell the two apart
+  static const char* train_names[3] = {"fno_epi_fwd_train_mma_bf16", "fno_epi_fwd_train_mma_bf16x3",
+                                       "fno_epi_fwd_train_mma_tf32"};
+  const int pv = TF ? 2 : (SPLIT ? 1 : 0);
+  const char* name = (MODE == EPI_FWD && k.a.gp) ? train_names[pv] : names[pv][MODE];
+  FNO_LAUNCH(name, (k_epi_mma<MODE, SPLIT, TF>), (int)g, kThreads, smem, s, k);
   return cudaSuccess;
 }
 

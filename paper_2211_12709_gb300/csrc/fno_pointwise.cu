@@ -867,7 +867,7 @@ cudaError_t launch_pointwise_bwd(const float* x, const float* w, const float* bi
 
 // tensor-core form of the pass (k_da_mma): staged rows, stages (two when two
 // CTAs per SM still fit), shared-memory bytes
-static bool da_mma_fits(int Ci, int Co) { return Ci + 1 <= 16 * kDaMT && Co <= 8 * kDaNT; }
+bool pointwise_da_mma_fits(int Ci, int Co) { return Ci + 1 <= 16 * kDaMT && Co <= 8 * kDaNT; }
 static void da_mma_plan(int Ci, int Co, int& nstage, size_t& smem) {
   const size_t stage = sizeof(float) * (size_t)(Ci + 1 + 2 * Co) * kPwLd;
   nstage = (2 * stage <= 110 * 1024) ? 2 : 1;
@@ -912,7 +912,7 @@ static cudaError_t launch_da_mma(const float* x, const float* g, const float* dz
 cudaError_t launch_pointwise_bwd_saved(const float* x, const float* g, const float* dz, float* da,
                                        float* part, int max_rows, int64_t B, int64_t P, int Ci,
                                        int Co, int* rows_out, cudaStream_t s) {
-  if (da_mma_fits(Ci, Co))
+  if (pointwise_da_mma_fits(Ci, Co))
     return launch_da_mma(x, g, dz, da, part, max_rows, B, P, Ci, Co, rows_out, s);
   // wider layers: the FP32 pair-block contraction of k_pw_bwd
   const PwPlan pl = pw_plan(Ci, Co, true);

@@ -75,6 +75,9 @@ TRAIN_CASES = [
     (Dims(2, 3, 2, 5, 7, 3, 7, 2, 3, 1, 4), "odd N: 4-byte staged copies"),
     # past 31 inputs or 24 outputs the dA pass contracts dW_lin on the CUDA cores
     (Dims(1, 40, 36, 6, 4, 16, 16, 2, 2, 4, 6), "40 -> 36 channels: the FP32 dA pass"),
+    # 32 channels: the tensor-core precisions keep the tensor-core dA epilogue
+    # (no GELU'(A) stored), FP32 takes the FP32 dA pass
+    (Dims(1, 32, 32, 4, 4, 16, 16, 2, 2, 4, 6), "32 channels: dA epilogue in the tensor-core precisions"),
 ]
 
 
