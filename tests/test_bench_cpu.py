@@ -1,0 +1,74 @@
+"""Host checks of bench.py's roofline bookkeeping (no GPU).
+
+The bench reports, for the dominant kernel, algorithmic bytes over the
+kernel's event time and DRAM traffic scaled from an ncu capture.  Both are
+keyed by the launch names the library gives its kernels, so a renamed launch
+would silently drop them: every traffic entry must name a launch the library
+makes, and every heavy launch must have an algorithmic byte count.
+"""
+import importlib.util
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# the bench workload: B 1, width 20, 128^3 x 32, modes 12/12/8/8
+DD = {"B": 1, "Ci": 20, "Co": 20, "Nx": 128, "Ny": 128, "Nz": 128, "Nt": 32,
+      "Jx": 24, "Jy": 24, "Jz": 16, "Jt": 8}
+GRID = 4 * 1 * 20 * 128 ** 3 * 32  # bytes of one FP32 activation tensor
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def launch_names():
+    names = set()
+    for p in glob.glob(os.path.join(ROOT, "paper_2211_12709_gb300", "csrc", "*.cu")):
+        names.update(re.findall(r'"(fno_[a-z0-9_]+)"', open(p).read()))
+    return names
+
+
+def test_traffic_entries_name_launches_of_the_library():
+    b = _bench()
+    names = launch_names()
+    assert "fno_da_saved" in names and "fno_epi_fwd_train_mma_bf16x3" in names
+    for key in b.TRAFFIC_PER_UNIT:
+        assert key in names, key
+
+
+def test_every_heavy_launch_has_algorithmic_bytes():
+    b = _bench()
+    heavy = [n for n in launch_names()
+             if n.startswith(("fno_epi_fwd", "fno_epi_da", "fno_epi_dx", "fno_fwd_tz", "fno_da_saved",
+                              "fno_mix"))]
+    assert len(heavy) >= 20
+    for n in heavy:
+        nbytes, _ = b.algorithmic(n, DD)
+        # every one moves at least one activation tensor, except the mixing
+        # kernels, which move the weights and the kept spectra
+        assert nbytes and nbytes > (0 if n.startswith("fno_mix") else GRID), n
+
+
+def test_training_forward_counts_the_derivative_store():
+    b = _bench()
+    train, _ = b.algorithmic("fno_epi_fwd_train_mma_bf16x3", DD)
+    plain, _ = b.algorithmic("fno_epi_fwd_mma_bf16x3", DD)
+    assert train - plain == GRID
+    # the dA pass reads x, dz and GELU'(A) and writes dA
+    assert b.algorithmic("fno_da_saved", DD)[0] == 4 * GRID
+
+
+def test_roofline_fraction_is_algorithmic_bytes_over_time_over_peak():
+    b = _bench()
+    pk = {"hbm_gbs": 6754.1, "bf16_tflops": 1929.9, "sm_max_mhz": 2070.0, "src": "measured"}
+    r = b.roofline_of("fno_da_saved", 4.94, DD, pk, "bf16x3")
+    achieved = 4 * GRID / 4.94e-3 / 1e9
+    assert r["bound"] == "hbm"
+    assert abs(r["achieved"] - achieved) < 0.5
+    assert abs(r["frac"] - achieved / 6754.1) < 1e-3
+    assert r["traffic"] is not None and abs(r["traffic"] / (4 * GRID) - 1) < 0.05
