@@ -172,7 +172,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t err;  // device status word (nonzero: a bounded wait gave up)
   size_t tab[10];
-  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, gp, total;
+  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, tc_tab, gp, total;
   bool da_in_dx;
 };
 
@@ -216,6 +216,8 @@ static Layout layout(const Dims& d, int op) {
   }
   L.mma_tab = off;  // basis fragments of the mma.sync epilogue
   off += align256(epilogue_mma_table_bytes(d));
+  L.tc_tab = off;  // z basis images of the tcgen05 epilogue
+  off += align256(epilogue_tc_table_bytes(d));
   if (op == FNO_OP_BLOCK_TRAIN) {
     L.gp = off;  // GELU'(A) of the training forward, [B][C_out][grid]
     off += align256(sizeof(float) * (size_t)(d.B * d.Co * d.Ng));
@@ -285,11 +287,14 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
   return FNO_OK;
 }
 
-// The fused inverse z, t + epilogue stage: warp-level mma.sync (BF16 or split
-// BF16) for the tensor-core precisions where its tiling applies, else FP32 on
+// The fused inverse z, t + epilogue stage, for the tensor-core precisions on
+// tcgen05 (TMEM accumulators) where its tiling applies, then on warp-level
+// mma.sync (the dA mode and the shapes tcgen05 does not tile), else FP32 on
 // the CUDA cores (the plain form, and the exact fallback for other shapes).
 static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base, const Layout& L,
                             int* err, int* grid_used, cudaStream_t s) {
+  if (is_tc(precision) && epilogue_tc_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
+    return launch_epilogue_tc(d, a, is_split(precision), precision == FNO_TF32, base + L.tc_tab, err, s);
   if (is_tc(precision) && epilogue_mma_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
     return launch_epilogue_mma(d, a, is_split(precision), precision == FNO_TF32, base + L.mma_tab, err,
                                grid_used, s);

@@ -93,6 +93,15 @@ size_t epilogue_mma_table_bytes(const Dims& d);
 cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, bool tf32, void* table,
                                 int* err, int* grid_used, cudaStream_t s);
 
+// Inverse z, t + epilogue on the 5th-generation tensor cores (fno_tc.cu):
+// tcgen05.mma into TMEM accumulators, modes EPI_FWD, EPI_DX and EPI_SPECTRAL;
+// same contract as launch_epilogue_f32 (no partial sums).  table: device
+// scratch of epilogue_tc_table_bytes(d) for the z basis images.
+bool epilogue_tc_supported(const Dims& d, int mode, int Cs, int Cl, char* why, size_t nwhy);
+size_t epilogue_tc_table_bytes(const Dims& d);
+cudaError_t launch_epilogue_tc(const Dims& d, const EpiArgs& a, bool split, bool tf32, void* table, int* err,
+                               cudaStream_t s);
+
 // One complex DFT axis on mma.sync (fno_mma.cu), BF16 (one product), split
 // BF16 (three-way splits, six products) or TF32 (operands rounded to TF32, then
 // split); same contract as launch_line_f32.

@@ -886,8 +886,8 @@ static cudaError_t launch_mma_m(const EpiM& k, bool split, bool tf32, int* g, cu
 
 // Tensor map of a [rows][chan] FP32 array with boxes of box_rows x 128 points,
 // encoded through the driver entry point (no link-time driver dependency).
-static cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long chan, long long rows,
-                                int box_rows) {
+cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long chan, long long rows,
+                         int box_rows) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                 CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
