@@ -64,8 +64,7 @@ typedef struct fno_dims {
  *               (nearest), exact products; a TF32 value is exact as BF16
  *               hi + lo, so it runs as split products on the BF16 tensor
  *               cores (the cost of FNO_BF16X3, the accuracy of TF32)
- *   FNO_BF16    BF16 tensor-core products (one product) in the DFT stages;
- *               the 1x1 of the fused tcgen05 epilogue as one TF32 product
+ *   FNO_BF16    BF16 tensor-core products (one product)
  *   FNO_BF16X3  split BF16 on the tensor cores: hi + lo with three products
  *               in the DFT stages, three-way splits with six products in the
  *               line stages and the mma.sync 1x1 stages; the 1x1 of the fused
@@ -73,10 +72,11 @@ typedef struct fno_dims {
  *               products), FP32-like
  * The tensor-core precisions need Nt even and at most 128, Nz * Nt a multiple
  * of 4, mt <= 8 and 2 mz <= 64 (FNO_ERR_UNSUPPORTED otherwise).  The fused
- * inverse z, t + epilogue stage runs on tcgen05 (TMEM accumulators) for Nt =
- * 16 or 32, Nz a multiple of 512 / Nt, 2 mz <= 24 and up to 32 channels, on
- * warp-level mma.sync for the other shapes its tiling takes (and for the dA
- * pass of fno_block_bwd), and on the FP32 kernels otherwise. */
+ * inverse z, t + epilogue stage runs, in FNO_BF16X3 and FNO_TF32, on tcgen05
+ * (TMEM accumulators) for Nt = 16 or 32, Nz a multiple of 512 / Nt, 2 mz <= 24
+ * and up to 32 channels; on warp-level mma.sync for FNO_BF16, the other shapes
+ * its tiling takes and the dA pass of fno_block_bwd; and on the FP32 kernels
+ * otherwise. */
 typedef enum fno_precision {
   FNO_FP32 = 0,
   FNO_TF32 = 1,

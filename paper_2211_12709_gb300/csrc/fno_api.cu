@@ -287,14 +287,16 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
   return FNO_OK;
 }
 
-// The fused inverse z, t + epilogue stage, for the tensor-core precisions on
-// tcgen05 (TMEM accumulators) where its tiling applies, then on warp-level
-// mma.sync (the dA mode and the shapes tcgen05 does not tile), else FP32 on
-// the CUDA cores (the plain form, and the exact fallback for other shapes).
+// The fused inverse z, t + epilogue stage: split BF16 and TF32 on tcgen05 (TMEM
+// accumulators) where its tiling applies, then warp-level mma.sync (plain BF16,
+// the dA mode and the shapes tcgen05 does not tile), else FP32 on the CUDA
+// cores (the plain form, and the exact fallback for other shapes).
 static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base, const Layout& L,
                             int* err, int* grid_used, cudaStream_t s) {
-  if (is_tc(precision) && epilogue_tc_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
-    return launch_epilogue_tc(d, a, is_split(precision), precision == FNO_TF32, base + L.tc_tab, err, s);
+  // plain BF16 (one product, no split operands to build) measured faster on
+  // mma.sync; the split precisions on tcgen05
+  if (is_split(precision) && epilogue_tc_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
+    return launch_epilogue_tc(d, a, true, precision == FNO_TF32, base + L.tc_tab, err, s);
   if (is_tc(precision) && epilogue_mma_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
     return launch_epilogue_mma(d, a, is_split(precision), precision == FNO_TF32, base + L.mma_tab, err,
                                grid_used, s);

@@ -25,8 +25,8 @@
 // Warp roles (16 warps): 0 TMA producer (x tiles, basis slices, spectra);
 // 1 and 3 issue the 1x1 MMAs of the even and the odd tiles (1 also owns the
 // TMEM allocation); 2 issues the stage-1 and stage-2 MMAs; 4-7 build operands
-// in shared memory (x tile -> TF32 big and small parts, spectrum -> U', QT
-// (TMEM) -> stage-2 operand); 8-15 the epilogue.  The roles hand work over
+// (x tile -> TF32 big and small parts in TMEM, spectrum -> U', QT (TMEM) ->
+// stage-2 operand in shared memory); 8-15 the epilogue.  The roles hand work over
 // through mbarriers only.  A thread waits about 60-170 SM cycles between two
 // tcgen05.mma it issues (measured), while the SM accepts one every ~40
 // cycles at N <= 64, so three threads issue and every descriptor is formed
@@ -34,10 +34,11 @@
 //
 // Precision.  Split BF16: stages 1 and 2 as hi + lo with three products
 // (hi.hi + hi.lo + lo.hi); the 1x1 as 3xTF32 (x = big + small, W likewise,
-// big.big + big.small + small.big), FP32-like.  BF16: one product in stages 1
-// and 2, one TF32 product in the 1x1.  TF32: operands rounded to TF32, then
-// stages 1 and 2 as split BF16 (exact for TF32 values up to the lo.lo term)
-// and one TF32 product in the 1x1.
+// big.big + big.small + small.big), FP32-like.  TF32: operands rounded to
+// TF32, then stages 1 and 2 as split BF16 (exact for TF32 values up to the
+// lo.lo term) and one TF32 product in the 1x1.  (The kernel also has a one-
+// product BF16 form; the library runs plain BF16 on the mma.sync epilogue,
+// which measured faster for it.)
 //
 // Every wait is bounded (about 2 s of SM clocks) and watches a CTA abort flag:
 // a role that gives up raises it and the error word, every role then leaves
@@ -64,9 +65,11 @@ namespace {
 
 constexpr int kTP = 128;         // points per tile = TMEM lanes
 constexpr int kGT = 4;           // tiles per group
-constexpr int kTcWarps = 16;
-constexpr int kTcThreads = 32 * kTcWarps;
-constexpr int kWProd = 0, kWIssA = 1, kWIssB = 2, kWIssA2 = 3, kWConv = 4, kWEpi = 8;
+constexpr int kWProd = 0, kWIssA = 1, kWIssB = 2, kWIssA2 = 3, kWConv = 4;
+// four converter warps, one per TMEM lane quarter (two per quarter measured
+// slower: the extra warps took issue slots from the epilogue)
+constexpr int kConvWarps = 4;
+constexpr int kTcThreads = 32 * (kWConv + kConvWarps + 8);
 constexpr long long kTcWait = 4000000000LL;  // about 2 s of SM clocks per wait
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -100,13 +103,13 @@ struct EpiTc {
   uint32_t o_x, x_bytes;    // x ring: S stages of Cl x 128 FP32
   uint32_t o_u1, u1_bytes;  // staged spectrum of one column [Cs][Jz][Jt] complex
   uint32_t o_bz, bz_part;   // z basis: [slot 2][hi, lo]
-  uint32_t o_a1, a1_part;   // x operand: [buf 2][big, small] 128 x KL TF32
+  uint32_t o_a1;            // start of the zero-initialised operand buffers
   uint32_t o_b1, b1_part;   // W_lin operand: [big, small] N1 x KL TF32
   uint32_t o_us, us_part;   // spectrum operand U': [hi, lo] (nMB 128) x KZ1 BF16
   uint32_t o_tb, tb_part;   // t basis band: [hi, lo] (256 - Nt) x 16 BF16
   uint32_t o_b2, b2_part;   // stage-2 operand: [hi, lo][plane ZB] N2 x 16 BF16
   uint32_t o_bias, o_bar, smem;
-  uint32_t t_d1, t_d2, t_qt, tcols;
+  uint32_t t_d1, t_d2, t_qt, t_a1, a1_cols, tcols;
 };
 
 // One bounded wait by the calling thread, also ending when the CTA aborts.
@@ -132,6 +135,7 @@ __device__ __forceinline__ bool tc_wait_warp(uint64_t* bar, uint32_t parity, vol
 template <int MODE, bool SPLIT, bool X3, bool TF, int CH>
 __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant__ EpiTc k) {
   constexpr bool LIN = MODE != EPI_SPECTRAL;
+  constexpr int NCV = kConvWarps, kWEpi = kWConv + NCV;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const EpiArgs& a = k.a;
@@ -173,14 +177,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
   if (tid == 0) {
     for (int i = 0; i < S; ++i) {
       tma::mbar_init(&xfull[i], 1);
-      tma::mbar_init(&xempty[i], 4);
+      tma::mbar_init(&xempty[i], NCV);
     }
     tma::mbar_init(u1full, 1);
-    tma::mbar_init(u1empty, 4);
+    tma::mbar_init(u1empty, NCV);
     for (int i = 0; i < 2; ++i) {
       tma::mbar_init(&bzfull[i], 1);
       tma::mbar_init(&bzempty[i], 1);
-      tma::mbar_init(&a1full[i], 4);
+      tma::mbar_init(&a1full[i], NCV);
       tma::mbar_init(&a1empty[i], 1);
       tma::mbar_init(&d1full[i], 1);
       tma::mbar_init(&d1empty[i], 8);
@@ -188,9 +192,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
       tma::mbar_init(&d2empty[i], 8);
     }
     for (int i = 0; i < 3; ++i) tma::mbar_init(&fin[i], 1);
-    tma::mbar_init(s1go, 4);
+    tma::mbar_init(s1go, NCV);
     tma::mbar_init(qtfull, 1);
-    tma::mbar_init(b2full, 4);
+    tma::mbar_init(b2full, NCV);
     tma::mbar_init(b2empty, 1);
     *s_abort = 0;
     tma::fence_mbar_init();
@@ -248,6 +252,80 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
   const long long g_end = k.ngroups * (blockIdx.x + 1) / gridDim.x;
   const int G = (int)(g_end - g_begin);
   auto col_of = [&](int gl) -> long long { return (g_begin + gl) / k.gpc; };
+
+  // QT (TMEM, rows (o, jt), columns (plane, re/im)) -> stage-2 operand B2, done
+  // by the converter warps (all planes of their TMEM lane quarter; converting in
+  // the epilogue warps measured slower).  Per thread, constant over the kernel:
+  // its row (o, jt) in each M-block and the B2 word offsets of that row in the
+  // four tiles' column blocks.
+  const int q = warp & 3;
+  bool qv[2];
+  uint32_t jrow[2][4];
+#pragma unroll
+  for (int mb = 0; mb < 2; ++mb) {
+    const int m = mb * kTP + 32 * q + lane, o = m >> 3, jt = m & 7;
+    qv[mb] = (mb < k.nMB) && (o < k.Cs);
+#pragma unroll
+    for (int j = 0; j < kGT; ++j)
+      jrow[mb][j] = qv[mb] ? umma::koff_bf16((uint32_t)(j * k.Cs + o), (uint32_t)(2 * jt), 256u) / 4u : 0u;
+  }
+  const uint32_t zstride = (uint32_t)k.N2 * 8u, lo_words = k.b2_part / 4u;
+  auto conv_qt = [&](int gl) -> bool {
+    if (!tc_wait_warp(qtfull, (uint32_t)(gl & 1), s_abort)) return false;
+    if (gl >= 1 && !tc_wait_warp(b2empty, (uint32_t)((gl - 1) & 1), s_abort)) return false;
+    umma::fence_after_sync();
+    uint32_t* b2 = reinterpret_cast<uint32_t*>(sm + k.o_b2);
+    // one (re, im) pair of plane pl = j ZB + zz: hi and lo BF16 pairs into B2
+    auto put = [&](int mb, int j, int zz, uint32_t re, uint32_t im) {
+      uint32_t h, l;
+      split2_bf16(rnd_tf<TF>(__uint_as_float(re)), rnd_tf<TF>(__uint_as_float(im)), h, l);
+      const uint32_t off = jrow[mb][j] + (uint32_t)zz * zstride;
+      b2[off] = h;
+      b2[lo_words + off] = l;
+    };
+#pragma unroll
+    for (int mb = 0; mb < 2; ++mb) {
+      if (mb >= k.nMB || mb * kTP + 32 * q >= k.Cs * 8) continue;  // uniform over the warp
+      const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + k.t_qt + (uint32_t)(mb * k.NS1);
+      if (k.ZB == 4) {
+        // 16 planes (4 tiles x 4 planes): 32 columns in two halves
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t v[16];
+          umma::tmem_ld16(ta + (uint32_t)(16 * hf), v);
+          umma::tmem_ld_wait();
+          if (qv[mb]) {
+#pragma unroll
+            for (int pp = 0; pp < 8; ++pp) {
+              const int pl = 8 * hf + pp;
+              put(mb, pl >> 2, pl & 3, v[2 * pp], v[2 * pp + 1]);
+            }
+          }
+        }
+      } else {
+        // 32 planes (4 tiles x 8 planes): 64 columns in two halves
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t v[32];
+          umma::tmem_ld16(ta + (uint32_t)(32 * hf), *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
+          umma::tmem_ld16(ta + (uint32_t)(32 * hf + 16), *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+          umma::tmem_ld_wait();
+          if (qv[mb]) {
+#pragma unroll
+            for (int pp = 0; pp < 16; ++pp) {
+              const int pl = 16 * hf + pp;
+              put(mb, pl >> 3, pl & 7, v[2 * pp], v[2 * pp + 1]);
+            }
+          }
+        }
+      }
+    }
+    umma::fence_before_sync();
+    tma::fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) tma::mbar_arrive(b2full);
+    return true;
+  };
 
   if (warp == kWProd) {
     // ======================= producer: TMA copies ===========================
@@ -333,9 +411,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
     const int bsel = (warp == kWIssA) ? 0 : 1;
     if (LIN && lane == 0 && G > 0) {
       const uint32_t id1 = umma::idesc(umma::kFmtTF32, kTP, k.N1);
-      // descriptors advance by 16-byte units in their address field
-      const uint64_t abig = umma::sdesc(s_base + k.o_a1 + (uint32_t)(2 * bsel) * k.a1_part, 128u, k.sbo_a1);
-      const uint64_t asmall = abig + (k.a1_part >> 4);
+      // the x operand in TMEM (lane = point, column = channel): [buf][big, small];
+      // B descriptors advance by 16-byte units in their address field
+      const uint32_t abig = tbase + k.t_a1 + (uint32_t)bsel * k.a1_cols, asmall = abig + (uint32_t)k.KL;
       const uint64_t bbig = umma::sdesc(s_base + k.o_b1, 128u, k.sbo_b1);
       const uint64_t bsmall = bbig + (k.b1_part >> 4);
       const uint32_t d = tbase + k.t_d1 + (uint32_t)(bsel * k.N1);
@@ -351,10 +429,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
         umma::fence_after_sync();
         for (int ks = 0; ks < nks; ++ks) {
           const uint64_t ko = (uint64_t)(ks * 16);
-          umma::mma_tf32(d, abig + ko, bbig + ko, id1, ks > 0 ? 1u : 0u);
+          const uint32_t ka = (uint32_t)(ks * 8);
+          umma::mma_tf32_ts(d, abig + ka, bbig + ko, id1, ks > 0 ? 1u : 0u);
           if (X3) {
-            umma::mma_tf32(d, abig + ko, bsmall + ko, id1, 1u);
-            umma::mma_tf32(d, asmall + ko, bbig + ko, id1, 1u);
+            umma::mma_tf32_ts(d, abig + ka, bsmall + ko, id1, 1u);
+            umma::mma_tf32_ts(d, asmall + ka, bbig + ko, id1, 1u);
           }
         }
         umma::commit(&d1full[bsel]);
@@ -429,8 +508,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
     }
   } else if (warp < kWEpi) {
     // ======================= operand converters =============================
-    const int ct = tid - 32 * kWConv;  // 0..127
-    const int q = warp & 3;            // this warp's TMEM lane quarter
+    const int ct = tid - 32 * kWConv;  // 0 .. 32 NCV - 1
     bool ok = true;
     int u1_use = 0;
     // U'[(o, jt)][(jz, re/im)] from the staged spectrum [o][jz][jt]
@@ -439,8 +517,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
       ++u1_use;
       const float2* u1s = reinterpret_cast<const float2*>(sm + k.o_u1);
       uint32_t* us = reinterpret_cast<uint32_t*>(sm + k.o_us);
-      // this thread's (jz, jt) items: r = ct and ct + 128 (Jz Jt <= 192)
-      for (int r = ct; r < k.JZT; r += 128) {
+      // this thread's (jz, jt) items r = ct, ct + 32 NCV, ... (Jz Jt <= 192)
+      for (int r = ct; r < k.JZT; r += 32 * NCV) {
         const int jz = r / k.Jt, jt = r - jz * k.Jt;
         uint32_t off = umma::koff_bf16((uint32_t)jt, (uint32_t)(2 * jz), k.sbo_u) / 4u;
         const float2* src = u1s + r;
@@ -459,77 +537,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
       if (lane == 0) tma::mbar_arrive(u1empty);
       return true;
     };
-    // QT (TMEM, rows (o, jt), columns (plane, re/im)) -> stage-2 operand B2
-    auto conv_qt = [&](int gl) -> bool {
-      if (!tc_wait_warp(qtfull, (uint32_t)(gl & 1), s_abort)) return false;
-      if (gl >= 1 && !tc_wait_warp(b2empty, (uint32_t)((gl - 1) & 1), s_abort)) return false;
-      umma::fence_after_sync();
-      uint32_t* b2 = reinterpret_cast<uint32_t*>(sm + k.o_b2);
-      for (int mb = 0; mb < k.nMB; ++mb) {
-        const int row0 = mb * kTP + 32 * q;
-        if (row0 >= k.Cs * 8) continue;  // uniform over the warp
-        const int m = row0 + lane, o = m >> 3, jt = m & 7;
-        const bool valid = o < k.Cs;
-        const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + k.t_qt + (uint32_t)(mb * k.NS1);
-        // row j Cs + o of plane zz's block = this lane's row o plus j Cs rows
-        const uint32_t rowoff = umma::koff_bf16((uint32_t)o, (uint32_t)(2 * jt), 256u) / 4u;
-        for (int ch = 0; ch < k.NS1 / 16; ++ch) {
-          uint32_t v[16];
-          umma::tmem_ld16(ta + (uint32_t)(16 * ch), v);
-          umma::tmem_ld_wait();
-          if (valid) {
-#pragma unroll
-            for (int pp = 0; pp < 8; ++pp) {
-              const int pl = 8 * ch + pp, j = pl >> k.zb_shift, zz = pl & (k.ZB - 1);
-              uint32_t h, l;
-              split2_bf16(rnd_tf<TF>(__uint_as_float(v[2 * pp])), rnd_tf<TF>(__uint_as_float(v[2 * pp + 1])), h, l);
-              const uint32_t off = ((uint32_t)zz * (uint32_t)k.N2 * 32u +
-                                    umma::koff_bf16((uint32_t)(j * k.Cs + o), 0u, 256u) -
-                                    umma::koff_bf16((uint32_t)o, 0u, 256u)) / 4u + rowoff;
-              b2[off] = h;
-              b2[k.b2_part / 4u + off] = l;
-            }
-          }
-        }
-      }
-      umma::fence_before_sync();
-      tma::fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) tma::mbar_arrive(b2full);
-      return true;
-    };
-    // x tile (FP32 [Cl][128]) -> 1x1 operand A1[buf]: row = point, K = channel
+    // x tile (FP32 [Cl][128]) -> the 1x1's A operand in TMEM, buffer t & 1: this
+    // thread's point p = 32 q + lane is TMEM lane p; column = channel (TF32 big,
+    // then small)
     auto conv_x = [&](int t) -> bool {
       const int s = t % S, n = t / S, bsel = t & 1;
       if (!tc_wait_warp(&xfull[s], (uint32_t)(n & 1), s_abort)) return false;
       if (t >= 2 && !tc_wait_warp(&a1empty[bsel], (uint32_t)(((t >> 1) - 1) & 1), s_abort)) return false;
+      umma::fence_after_sync();
       const float* xs = reinterpret_cast<const float*>(sm + k.o_x + (size_t)s * k.x_bytes);
-      unsigned char* ab = sm + k.o_a1 + (size_t)(2 * bsel) * k.a1_part;
-      const int p = ct;
-      float v[32];
+      const int p = 32 * q + lane;
+      const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + k.t_a1 + (uint32_t)bsel * k.a1_cols;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        // rows past Cl read the last row and are zeroed by a select (no branch)
-        const float xv = xs[(size_t)min(i, k.Cl - 1) * kTP + p];
-        v[i] = (i < k.Cl) ? xv : 0.f;
-      }
-      const uint32_t off0 = umma::koff_tf32((uint32_t)p, 0u, k.sbo_a1);
+      for (int c8 = 0; c8 < 4; ++c8) {
+        if (8 * c8 < k.KL) {
+          uint32_t big[8], small[8];
 #pragma unroll
-      for (int i4 = 0; i4 < 8; ++i4) {
-        if (4 * i4 < k.KL) {
-          float4 big;
-          big.x = tf32_rna(v[4 * i4]);
-          big.y = tf32_rna(v[4 * i4 + 1]);
-          big.z = tf32_rna(v[4 * i4 + 2]);
-          big.w = tf32_rna(v[4 * i4 + 3]);
-          const uint32_t off = off0 + (uint32_t)i4 * 128u;
-          *reinterpret_cast<float4*>(ab + off) = big;
-          if (X3)
-            *reinterpret_cast<float4*>(ab + k.a1_part + off) =
-                make_float4(v[4 * i4] - big.x, v[4 * i4 + 1] - big.y, v[4 * i4 + 2] - big.z, v[4 * i4 + 3] - big.w);
+          for (int r = 0; r < 8; ++r) {
+            // rows past Cl read the last row and are zeroed by a select (no branch)
+            const int i = 8 * c8 + r;
+            const float xv = xs[(size_t)min(i, k.Cl - 1) * kTP + p];
+            const float v = (i < k.Cl) ? xv : 0.f;
+            const float bg = tf32_rna(v);
+            big[r] = __float_as_uint(bg);
+            small[r] = __float_as_uint(v - bg);
+          }
+          umma::tmem_st8(ta + (uint32_t)(8 * c8), big);
+          if (X3) umma::tmem_st8(ta + (uint32_t)(k.KL + 8 * c8), small);
         }
       }
-      tma::fence_proxy_async();
+      umma::tmem_st_wait();
+      umma::fence_before_sync();
       __syncwarp();
       if (lane == 0) {
         tma::mbar_arrive(&a1full[bsel]);
@@ -537,30 +575,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
       }
       return true;
     };
-    auto go_s1 = [&]() {
+    // Arrivals carry no phase, so a warp arrives on s1go for phase p only once
+    // phase p - 1 has completed; otherwise a warp running ahead would complete
+    // phase p - 1 early, before a slower warp had written its part of U'.
+    auto go_s1 = [&](int p) -> bool {
+      if (p > 0 && !tc_wait_warp(s1go, (uint32_t)((p - 1) & 1), s_abort)) return false;
       __syncwarp();
       if (lane == 0) tma::mbar_arrive(s1go);
+      return true;
+    };
+    // the stage-1 operand U' of group p; a new column's U' is built once S1 of
+    // group p - 1 has read the previous one (qtfull phase p - 1)
+    auto stage1_operand = [&](int p) -> bool {
+      if (p > 0 && col_of(p) == col_of(p - 1)) return go_s1(p);
+      if (p > 0 && !tc_wait_warp(qtfull, (uint32_t)((p - 1) & 1), s_abort)) return false;
+      if (!build_us()) return false;
+      return go_s1(p);
     };
     if (G > 0) {
-      // stage-1 operand of group 0 and 1; stage-2 operand of group 0
-      ok = build_us();
-      if (ok) go_s1();
+      ok = stage1_operand(0);
       ok = ok && conv_qt(0);
-      if (ok && G > 1) {
-        if (col_of(1) != col_of(0)) ok = build_us();
-        if (ok) go_s1();
-      }
-      // per group gl: its first x tile, the stage-2 operand of gl + 1 (and the
-      // stage-1 operand of gl + 2), then its other x tiles
+      if (ok && G > 1) ok = stage1_operand(1);
+      // per group gl: its first x tile, the stage-2 operand of gl + 1, the
+      // stage-1 operand of gl + 2, its other x tiles
       for (int gl = 0; ok && gl < G; ++gl) {
         if (LIN) ok = conv_x(kGT * gl);
-        if (ok && gl + 1 < G) {
-          ok = conv_qt(gl + 1);
-          if (ok && gl + 2 < G) {
-            if (col_of(gl + 2) != col_of(gl + 1)) ok = build_us();
-            if (ok) go_s1();
-          }
-        }
+        if (ok && gl + 1 < G) ok = conv_qt(gl + 1);
+        if (ok && gl + 2 < G) ok = stage1_operand(gl + 2);
         if (LIN)
           for (int j = 1; ok && j < kGT; ++j) ok = conv_x(kGT * gl + j);
       }
@@ -568,7 +609,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_epi_tc(const __grid_constant_
     }
   } else {
     // ======================= epilogue =======================================
-    const int q = warp & 3, h = (warp - kWEpi) >> 2;
+    const int h = (warp - kWEpi) >> 2;
     const int p = 32 * q + lane;
     const int c_lo = h * k.Ch;
     const int nc = min(k.Ch, k.Cs - c_lo);
@@ -714,7 +755,10 @@ static bool tc_plan(const Dims& d, int mode, int Cs, int Cl, EpiTc& k, char* why
   k.t_d1 = 0;
   k.t_d2 = (uint32_t)(2 * k.N1);
   k.t_qt = k.t_d2 + (uint32_t)(2 * k.N2);
-  uint32_t need = k.t_qt + (uint32_t)(k.nMB * k.NS1);
+  k.t_a1 = k.t_qt + (uint32_t)(k.nMB * k.NS1);
+  // the x operand of the 1x1: two buffers of KL TF32 columns (big, and small in split BF16)
+  k.a1_cols = lin ? (uint32_t)(k.KL * 2) : 0u;
+  uint32_t need = k.t_a1 + 2u * k.a1_cols;
   need = std::max(need, k.t_d2 + (uint32_t)(k.N2 + (kGT - 1) * Cs + k.Ch + 16));
   k.tcols = 32;
   while (k.tcols < need) k.tcols <<= 1;
@@ -724,7 +768,6 @@ static bool tc_plan(const Dims& d, int mode, int Cs, int Cl, EpiTc& k, char* why
   k.x_bytes = x_bytes;
   k.u1_bytes = (uint32_t)(Cs * k.JZT * 8);
   k.bz_part = (uint32_t)(k.NS1 * k.KZ1 * 2);
-  k.a1_part = lin ? (uint32_t)(kTP * k.KL * 4) : 0u;
   k.b1_part = lin ? (uint32_t)(k.N1 * k.KL * 4) : 0u;
   k.us_part = (uint32_t)(k.nMB * kTP * k.KZ1 * 2);
   k.tb_part = (uint32_t)((2 * kTP - k.Nt) * 16 * 2);
@@ -738,7 +781,6 @@ static bool tc_plan(const Dims& d, int mode, int Cs, int Cl, EpiTc& k, char* why
     k.o_bz = o;
     o = al128(o + 4u * k.bz_part);
     k.o_a1 = o;  // zero-initialised from here to o_bias
-    o = al128(o + 4u * k.a1_part);
     k.o_b1 = o;
     o = al128(o + 2u * k.b1_part);
     k.o_us = o;
@@ -770,7 +812,6 @@ static bool tc_plan(const Dims& d, int mode, int Cs, int Cl, EpiTc& k, char* why
   if ((uint32_t)(k.ZB - 1) * (uint32_t)k.N2 * 32u + span((uint32_t)k.N2, 256u) > k.b2_part)
     return no("stage-2 B operand extent");
   if (lin) {
-    if ((uint32_t)(k.KL / 8 - 1) * 256u + span(kTP, k.sbo_a1) > k.a1_part) return no("1x1 A operand extent");
     if ((uint32_t)(k.KL / 8 - 1) * 256u + span((uint32_t)k.N1, k.sbo_b1) > k.b1_part)
       return no("1x1 B operand extent");
   }
