@@ -57,7 +57,6 @@ STACKS = {
 DEFAULT_WORKLOAD = "co2_block_128c_t32"
 METRIC = "spectral block fwd+bwd Gpoint·ch/s & roofline %, BF16/split vs FP32 @ stated err"
 UNIT = "Gpoint*ch/s"
-CPU_SAMPLE_CHANNELS = 4
 
 
 def peaks():
@@ -225,12 +224,54 @@ def roofline_of(name, per_launch_ms, dd, pk, precision):
     return out
 
 
-def precision_sweep(args, step_of, outs, stream, barrier, units):
-    """Time the other precisions on the resident inputs; rel-L2 of every result vs FP32."""
+def sample_points(grid, n, seed):
+    """n grid points (x, y, z, t): the two ends of every axis through the centre,
+    the first and the last corner, then seeded random points."""
+    import numpy as np
+    g = np.random.Generator(np.random.PCG64(seed))
+    pts = np.stack([g.integers(0, s, n) for s in grid], axis=1)
+    edges = []
+    for a, s in enumerate(grid):
+        for v in (0, s - 1):
+            p = [s2 // 2 for s2 in grid]
+            p[a] = v
+            edges.append(p)
+    edges.append([0, 0, 0, 0])
+    edges.append([s - 1 for s in grid])
+    return np.concatenate([np.array(edges, dtype=np.int64), pts.astype(np.int64)])[:n]
+
+
+def oracle_reference(dims, x, w, wl, b, dz, pts):
+    """The FP64 oracle's block forward and backward on the same inputs: z and dx at
+    the sampled points, dw, dw_lin and db in full (the kept spectra are exact)."""
+    import oracle
+    _, zp = oracle.block_fwd(dims, x, w, wl, b, full=False, pts=pts)
+    r = oracle.block_bwd(dims, x, w, dz, wl, b, full=False, pts=pts)
+    return {"z": zp, "dx": r["dx_pts"], "dw": r["dw"], "dw_lin": r["dwl"], "db": r["db"]}
+
+
+def errors_vs_oracle(ref, outs, pts):
+    """rel-L2 per tensor of the GPU results against the oracle reference."""
+    import numpy as np
+    import torch
+    z, dx, dw, dwl, db = outs
+    ix = [torch.from_numpy(pts[:, a]).to(z.device) for a in range(4)]
+    got = {"z": z[:, :, ix[0], ix[1], ix[2], ix[3]], "dx": dx[:, :, ix[0], ix[1], ix[2], ix[3]],
+           "dw": dw, "dw_lin": dwl, "db": db}
+    out = {}
+    for k, r in ref.items():
+        a = got[k].detach().double().cpu().numpy().ravel()
+        out[k] = float(np.linalg.norm(a - r.ravel()) / np.linalg.norm(r.ravel()))
+    return out
+
+
+def precision_sweep(args, step_of, outs, stream, barrier, units, ref=None, pts=None):
+    """Time every precision on the resident inputs; rel-L2 of every result against
+    the FP64 oracle (ref, at the sampled points pts) and against the FP32 plain form."""
     import torch
     ref_prec = "fp32"
     runs = {}
-    ref = None
+    ref32 = None
     for prec in ["fp32", "tf32", "bf16", "bf16x3"]:
         st = step_of(prec)
         for _ in range(3):
@@ -246,16 +287,18 @@ def precision_sweep(args, step_of, outs, stream, barrier, units):
         ms = a.elapsed_time(b) / args.steps
         res = [t.detach().double().clone() if prec == ref_prec else t.detach().double() for t in outs]
         if prec == ref_prec:
-            ref = res
+            ref32 = res
             err = None
         else:
             err = {k: float(torch.linalg.vector_norm(r - q) / torch.linalg.vector_norm(q))
-                   for k, r, q in zip(("z", "dx", "dw", "dw_lin", "db"), res, ref)}
+                   for k, r, q in zip(("z", "dx", "dw", "dw_lin", "db"), res, ref32)}
         runs[prec] = {"ms_per_step": round(ms, 3), "value": units / (ms * 1e-3) / 1e9,
+                      "rel_l2_vs_oracle": errors_vs_oracle(ref, outs, pts) if ref is not None else None,
                       "rel_l2_vs_fp32": err}
         del res
-    runs["note"] = ("FP32 plain form vs the FP64 oracle: rel-L2 ~1e-7 in the parity tests; "
-                    "tolerances vs the oracle: fp32 and bf16x3 1e-5, tf32 5e-3, bf16 2e-2")
+    runs["tolerance_vs_oracle"] = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-2, "tf32": 5e-3}
+    runs["note"] = ("rel-L2 vs the FP64 oracle: z and dx at the sampled points, dw, dw_lin, db "
+                    "in full; the tf32 bound is ten TF32-rounded operands on a path (2^-11 each)")
     return runs
 
 
@@ -279,28 +322,36 @@ def whole_job_value(units_per_rank: int, world: int, ms: float) -> float:
     return units_per_rank * world / (ms * 1e-3) / 1e9
 
 
-def oracle_sample_time(wl_name, sample_channels, seed=1000):
-    """Seconds of one oracle fwd+bwd on the workload grid with fewer channels, and its units."""
-    import numpy as np
+# The CPU baseline times the whole oracle block fwd + bwd (kept spectra, mixing,
+# the z synthesis, 1x1, bias, GELU, and every gradient including the dX synthesis
+# with its W_lin dA term) with every channel of the workload, on a bounded cut of
+# its grid: at most 64 x 32 x 32 cells in x, y, z, every time step, the same kept
+# modes.  About 5-10 s per pass on 16 host cores.
+CPU_SAMPLE_GRID = (64, 32, 32)
 
+
+def oracle_sample_time(wl_name, seed=1000):
+    """Seconds of one full oracle fwd+bwd on the bounded sample, its units and description."""
     import oracle
     from oracle import Dims
     from paper_2211_12709_gb300 import inputs
     B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[wl_name][:11]
-    c = min(C, sample_channels)
-    d = Dims(1, c, c, Nx, Ny, Nz, Nt, mx, my, mz, mt)
-    x = inputs.normal((1, c) + d.grid, seed)
-    w = inputs.spectral_weights(c, c, d.modes, seed + 1)
-    wl, b = inputs.linear_params(c, c, seed + 2)
-    dz = inputs.normal((1, c) + d.grid, seed + 3)
-    pts = np.array([[0, 0, 0, 0]])
+    nx, ny, nz = (min(n, c) for n, c in zip((Nx, Ny, Nz), CPU_SAMPLE_GRID))
+    d = Dims(1, C, C, nx, ny, nz, Nt, mx, my, mz, mt)
+    x = inputs.normal((1, C) + d.grid, seed)
+    w = inputs.spectral_weights(C, C, d.modes, seed + 1)
+    wl, b = inputs.linear_params(C, C, seed + 2)
+    dz = inputs.normal((1, C) + d.grid, seed + 3)
     cores = oracle.threads()
     t0 = time.perf_counter()
-    oracle.block_fwd(d, x, w, wl, b, full=False, pts=pts)
-    oracle.block_bwd(d, x, w, dz, wl, b, full=False, pts=pts)
+    oracle.block_fwd(d, x, w, wl, b, full=True)
+    oracle.block_bwd(d, x, w, dz, wl, b, full=True)
     dt = time.perf_counter() - t0
     units = d.B * d.Ci * d.n_grid
-    return dt, units, cores, f"B=1, C_in=C_out={c} on the {Nx}x{Ny}x{Nz}x{Nt} grid, modes {mx}/{my}/{mz}/{mt}"
+    sample = (f"the whole FP64 oracle block fwd+bwd (z and dX syntheses, 1x1, GELU, every gradient), "
+              f"B=1, C_in=C_out={C} (every channel), grid {nx}x{ny}x{nz}x{Nt} cut from "
+              f"{Nx}x{Ny}x{Nz}x{Nt}, modes {mx}/{my}/{mz}/{mt}")
+    return dt, units, cores, sample
 
 
 def stack_arrays(name, cfg, width=None, batch=None):
@@ -363,11 +414,11 @@ def run_reference(args, rank, world):
     wl_name = args.workload
     B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[wl_name][:11]
     if args.warmup > 0:  # one untimed oracle pass stands for the warm-up steps
-        oracle_sample_time(wl_name, CPU_SAMPLE_CHANNELS)
+        oracle_sample_time(wl_name)
     times = []
     units = cores = sample = None
     for _ in range(args.steps):
-        dt, units, cores, sample = oracle_sample_time(wl_name, CPU_SAMPLE_CHANNELS)
+        dt, units, cores, sample = oracle_sample_time(wl_name)
         times.append(dt)
     tot = sum(times)
     value = units * len(times) / tot / 1e9
@@ -509,6 +560,61 @@ def run_stack(args, rank, world, local, dev, dist):
     return 0
 
 
+SMALL_WORKLOAD = "ns_block_64c_t16"
+
+
+def workload_arrays(name, cfg):
+    """Seeded input, upstream gradient and parameters of a block workload (NumPy, FP32)."""
+    import numpy as np
+    from paper_2211_12709_gb300 import inputs
+    B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[name][:11]
+    n_distinct = WORKLOADS[name][11] if len(WORKLOADS[name]) > 11 else C
+    x = inputs.grf((B, n_distinct), (Nx, Ny, Nz, Nt), ell, inputs.SEED_INPUT + cfg)
+    if n_distinct < C:
+        x = np.tile(x, (1, (C + n_distinct - 1) // n_distinct, 1, 1, 1, 1))[:, :C].copy()
+    dz = inputs.normal((B, C, Nx, Ny, Nz, Nt), inputs.SEED_UPSTREAM + cfg)
+    w = inputs.spectral_weights(C, C, (2 * mx, 2 * my, 2 * mz, mt), inputs.SEED_SPECTRAL_W + cfg)
+    wl, b = inputs.linear_params(C, C, inputs.SEED_LINEAR + cfg)
+    return x, dz, w, wl, b
+
+
+def shape_sweep(name, args, dev, stream, barrier, cfg):
+    """The precision sweep (training forward + saved backward, every precision,
+    times and errors against the FP64 oracle) on another block workload."""
+    import torch
+    from oracle import Dims
+    from paper_2211_12709_gb300 import _lib, ops
+    B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[name][:11]
+    x_np, dz_np, w_np, wl_np, b_np = workload_arrays(name, cfg)
+    T = lambda a: torch.from_numpy(a).to(dev)
+    x, dz, w, wl, bias = T(x_np), T(dz_np), T(w_np), T(wl_np), T(b_np)
+    z, dx, dw, dwl, db = (torch.empty_like(t) for t in (x, x, w, wl, bias))
+    d = ops.dims_of(x, C, (mx, my, mz, mt))
+    nws = max(_lib.fno_workspace_bytes(d, ops.precision_code(q), ops.OP_BLOCK_TRAIN)
+              for q in ("fp32", "tf32", "bf16", "bf16x3"))
+    ws = torch.empty(nws, dtype=torch.uint8, device=dev)
+    sh = int(stream.cuda_stream)
+
+    def step_of(prec, saved=True):
+        pc = ops.precision_code(prec)
+
+        def st():
+            _lib.fno_block_fwd_train(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                                     z.data_ptr(), ws.data_ptr(), nws, sh)
+            _lib.fno_block_bwd_saved(d, pc, x.data_ptr(), w.data_ptr(), wl.data_ptr(), bias.data_ptr(),
+                                     dz.data_ptr(), dx.data_ptr(), dw.data_ptr(), dwl.data_ptr(),
+                                     db.data_ptr(), ws.data_ptr(), nws, sh)
+        return st
+
+    pts = sample_points((Nx, Ny, Nz, Nt), 96, 78)
+    ref = oracle_reference(Dims(B, C, C, Nx, Ny, Nz, Nt, mx, my, mz, mt), x_np, w_np, wl_np, b_np, dz_np, pts)
+    out = precision_sweep(args, step_of, (z, dx, dw, dwl, db), stream, barrier, B * C * Nx * Ny * Nz * Nt,
+                          ref, pts)
+    out["config"] = {"B": B, "C_in": C, "C_out": C, "grid": [Nx, Ny, Nz, Nt], "modes": [mx, my, mz, mt]}
+    del x, dz, z, dx, ws
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,19 +655,15 @@ def main():
         return run_stack(args, rank, world, local, dev, dist)
 
     B, C, Nx, Ny, Nz, Nt, mx, my, mz, mt, ell = WORKLOADS[args.workload][:11]
-    n_distinct = WORKLOADS[args.workload][11] if len(WORKLOADS[args.workload]) > 11 else C
     modes = (mx, my, mz, mt)
     Ng = Nx * Ny * Nz * Nt
     cfg = replica_seed(rank)
     # inputs in pinned host memory (the e2e leg copies them every step)
-    x_np = inputs.grf((B, n_distinct), (Nx, Ny, Nz, Nt), ell, inputs.SEED_INPUT + cfg)
-    if n_distinct < C:
-        x_np = np.tile(x_np, (1, (C + n_distinct - 1) // n_distinct, 1, 1, 1, 1))[:, :C].copy()
+    x_np, dz_np, w_np, wl_np, b_np = workload_arrays(args.workload, cfg)
     x_h = torch.from_numpy(x_np).pin_memory()
-    del x_np
-    dz_h = torch.from_numpy(inputs.normal((B, C, Nx, Ny, Nz, Nt), inputs.SEED_UPSTREAM + cfg)).pin_memory()
-    w = torch.from_numpy(inputs.spectral_weights(C, C, (2 * mx, 2 * my, 2 * mz, mt), inputs.SEED_SPECTRAL_W + cfg)).to(dev)
-    wl_np, b_np = inputs.linear_params(C, C, inputs.SEED_LINEAR + cfg)
+    dz_h = torch.from_numpy(dz_np).pin_memory()
+    del x_np, dz_np
+    w = torch.from_numpy(w_np).to(dev)
     wl, bias = torch.from_numpy(wl_np).to(dev), torch.from_numpy(b_np).to(dev)
     x = x_h.to(dev)
     dz = dz_h.to(dev)
@@ -721,15 +823,22 @@ def main():
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = roofline_of(top[0], top[1][1] / top[1][0], dd, pk, args.precision) if top else None
 
-    # ---- the other precisions on the same inputs: time and error vs the FP32 plain form ----
+    # ---- every precision on the same inputs: time, and error vs the FP64 oracle ----
     sweep = None
     if not args.no_sweep:
-        sweep = precision_sweep(args, step_of, (z, dx, dw, dwl, db), stream, barrier, units * world)
+        from oracle import Dims
+        od = Dims(B, C, C, Nx, Ny, Nz, Nt, mx, my, mz, mt)
+        pts = sample_points((Nx, Ny, Nz, Nt), 96, 77)
+        ref = oracle_reference(od, x_h.numpy(), w_np, wl_np, b_np, dz_h.numpy(), pts)
+        sweep = precision_sweep(args, step_of, (z, dx, dw, dwl, db), stream, barrier, units * world,
+                                ref, pts)
+        if args.workload != SMALL_WORKLOAD:
+            sweep[SMALL_WORKLOAD] = shape_sweep(SMALL_WORKLOAD, args, dev, stream, barrier, cfg)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            dt, u, cores, sample = oracle_sample_time(args.workload, CPU_SAMPLE_CHANNELS)
+            dt, u, cores, sample = oracle_sample_time(args.workload)
             cpu = {"value": u / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
         except Exception as ex:  # the baseline is reported, never required
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}

@@ -275,7 +275,12 @@ int fno_adam_step(int64_t n, float* param, const float* grad, float* m, float* v
  *     before anything is enqueued.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before capturing any stream.
+ *     before capturing any stream.  The lookup also loads the library's device
+ *     code on that device, which is when the array's memory is committed: a
+ *     host that reserves the rest of device memory up front calls
+ *     fno_static_prepare() first.
+ *   - The address is cached per device for the life of the process; it does
+ *     not survive cudaDeviceReset, so these calls must not be used across one.
  *   - All calls share the one array and it keeps the previous call's contents;
  *     every byte a call reads from it is written earlier in the same call, so
  *     nothing needs clearing.  Calls that overlap on the GPU (other streams,
@@ -284,6 +289,19 @@ int fno_adam_step(int64_t n, float* param, const float* grad, float* m, float* v
 #define FNO_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 int fno_spectral_fwd_static(const fno_dims* dims, int precision, const float* x, const float* w,
                             float* y, void* stream);
+
+/* Looks up the static scratch on the current device, loading the library's
+ * device code there (so committing the array's FNO_STATIC_SCRATCH_BYTES now
+ * rather than at the first fno_spectral_fwd_static).  No allocation call is
+ * made.  Returns FNO_OK or FNO_ERR_CUDA. */
+int fno_static_prepare(void);
+
+/* Status the last fno_spectral_fwd_static call on the current device left in
+ * the static scratch: waits for `stream`, then returns FNO_OK,
+ * FNO_ERR_TIMEOUT when one of that call's bounded device-side waits gave up,
+ * or FNO_ERR_CUDA when a kernel found its shared-memory window misaligned
+ * (the codes of fno_workspace_status). */
+int fno_static_status(void* stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ EXPORTS = (
     "fno_profile_stop", "fno_profile_count", "fno_profile_entry", "fno_spectral_fwd_static", "fno_workspace_status", "fno_last_status",
     "fno_pointwise_fwd", "fno_pointwise_workspace_bytes", "fno_pointwise_bwd",
     "fno_mse_workspace_bytes", "fno_mse_loss", "fno_block_bwd_saved", "fno_adam_step",
-    "fno_block_fwd_train",
+    "fno_block_fwd_train", "fno_static_prepare", "fno_static_status",
 )
 FNO_ACT_NONE, FNO_ACT_GELU = 0, 1
 FNO_STATIC_SCRATCH_BYTES = 16 << 20
@@ -76,6 +76,10 @@ def load(build_if_needed: bool = True):
         lib.fno_block_fwd_train.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_spectral_fwd_static.argtypes = [dp, ci, vp, vp, vp, vp]
         lib.fno_spectral_fwd_static.restype = ci
+        lib.fno_static_prepare.argtypes = []
+        lib.fno_static_prepare.restype = ci
+        lib.fno_static_status.argtypes = [vp]
+        lib.fno_static_status.restype = ci
         lib.fno_block_bwd.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.fno_block_bwd_saved.argtypes = [dp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         for f in (lib.fno_spectral_fwd, lib.fno_spectral_bwd, lib.fno_block_fwd, lib.fno_block_bwd,
@@ -145,6 +149,16 @@ def fno_spectral_fwd(dims, precision, x, w, y, ws, ws_bytes, stream=0):
 def fno_spectral_fwd_static(dims, precision, x, w, y, stream=0):
     """fno_spectral_fwd with the library's static device scratch (no workspace argument)."""
     _check(load().fno_spectral_fwd_static(ctypes.byref(dims), int(precision), x, w, y, stream))
+
+
+def fno_static_prepare():
+    """Load the library's device code on the current device (commits the static scratch)."""
+    _check(load().fno_static_prepare())
+
+
+def fno_static_status(stream=0):
+    """Raise FnoError if the last fno_spectral_fwd_static call left an error status."""
+    _check(load().fno_static_status(stream))
 
 
 def fno_spectral_bwd(dims, precision, x, w, dy, dx, dw, ws, ws_bytes, stream=0):

@@ -749,17 +749,22 @@ int fno_adam_step(int64_t n, float* param, const float* grad, float* m, float* v
   return FNO_OK;
 }
 
-int fno_workspace_status(const void* ws, void* stream) {
-  if (!ws) return fail(FNO_ERR_INVALID_ARG, "ws is NULL");
+// Reads the device status word at the start of a scratch area (a workspace or
+// the static scratch) once `stream` has drained, and decodes it.
+static int read_status_word(const void* word, cudaStream_t s) {
   int h = 0;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(&h, word, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(status)");
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   if (h == 2) return fail(FNO_ERR_CUDA, "a kernel refused a misaligned shared-memory window");
   if (h != 0) return fail(FNO_ERR_TIMEOUT, "a bounded device-side wait gave up (status %d)", h);
   return FNO_OK;
+}
+
+int fno_workspace_status(const void* ws, void* stream) {
+  if (!ws) return fail(FNO_ERR_INVALID_ARG, "ws is NULL");
+  return read_status_word(ws, (cudaStream_t)stream);
 }
 
 const char* fno_last_error(void) { return g_err.c_str(); }
@@ -829,7 +834,11 @@ static void* g_static_ptr[64] = {nullptr};
 
 // Device address of the static scratch on the current device.  The array's host
 // name is only a host-side stand-in, so the address is looked up once per
-// device with that device current and cached.
+// device with that device current and cached.  The lookup also loads the
+// library's device code on that device (modules load lazily), which is when
+// the array's memory is committed.  A cached address does not survive a reset
+// of the device (cudaDeviceReset): the entry points below must not be used
+// across one.
 static int static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -847,6 +856,18 @@ static int static_scratch(void** out) {
   return FNO_OK;
 }
 }  // namespace fno
+
+extern "C" int fno_static_prepare(void) {
+  void* ws = nullptr;
+  return fno::static_scratch(&ws);
+}
+
+extern "C" int fno_static_status(void* stream) {
+  void* ws = nullptr;
+  int rc = fno::static_scratch(&ws);
+  if (rc) return rc;
+  return read_status_word(ws, (cudaStream_t)stream);
+}
 
 extern "C" int fno_spectral_fwd_static(const fno_dims* dims, int precision, const float* x,
                                        const float* w, float* y, void* stream) {
