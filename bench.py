@@ -181,6 +181,8 @@ TRAFFIC_PER_UNIT = {
     "fno_da_saved": (2.013355e9 + 0.647265e9) / 167772160,
     "fno_epi_dx_mma_bf16x3": (0.800973e9 + 0.613033e9) / 167772160,
     "fno_fwd_tz_mma_bf16x3": (0.671163e9 + 0.112208e9) / 167772160,
+    "fno_epi_fwd_train_tc_bf16x3": (0.798249e9 + 1.285758e9) / 167772160,
+    "fno_epi_dx_tc_bf16x3": (0.798222e9 + 0.608979e9) / 167772160,
 }
 
 
