@@ -264,6 +264,15 @@ static cudaError_t line(const float2* in, float2* out, int64_t outer, int nin, i
   return launch_line_f32(in, out, outer, nin, nout, inner, tab, s);
 }
 
+// The y then x stages of a forward kept-mode spectrum, from the t, z spectra
+// t1 = [B][C][Nx][Ny][Jz][Jt] into out.  Uses t2.
+static int spectrum_yx(const Dims& d, int64_t C, const Tables& T, const float2* t1, float2* t2, float2* out,
+                       cudaStream_t s, int precision) {
+  CK(line(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, precision, s));
+  CK(line(t2, out, d.B * C, (int)d.Nx, (int)d.Jx, d.Jy * d.Jz * d.Jt, T.Fx, precision, s));
+  return FNO_OK;
+}
+
 // Forward kept-mode spectrum of C channels of src into out: t,z per column
 // (tensor cores for the BF16 precisions) -> y -> x.  Uses t1, t2.
 static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2* ft,
@@ -274,9 +283,7 @@ static int spectrum_f32(const Dims& d, int64_t C, const float* src, const float2
                          precision == FNO_TF32, err, s));
   else
     CK(launch_fwd_tz_f32(src, t1, d.B * C * d.Nx * d.Ny, d, ft, T.Fz, s));
-  CK(line(t1, t2, d.B * C * d.Nx, (int)d.Ny, (int)d.Jy, d.Jz * d.Jt, T.Fy, precision, s));
-  CK(line(t2, out, d.B * C, (int)d.Nx, (int)d.Jx, d.Jy * d.Jz * d.Jt, T.Fx, precision, s));
-  return FNO_OK;
+  return spectrum_yx(d, C, T, t1, t2, out, s, precision);
 }
 
 // Inverse x then y of C channels of kept spectra into u1 = [B][C][Nx][Ny][Jz][Jt].
@@ -586,11 +593,21 @@ static int block_bwd_impl(const fno_dims* dims, int precision, const float* x, c
     if ((rc = inverse_xy_f32(d, d.Co, yh, T, t2, t1, s, precision))) return rc;
   }
   int rows = 0;
+  bool tz_done = false;  // t1 already holds the t, z spectrum of dA
   if (train) {
-    // dA = dz GELU'(A) from the training forward's GELU'(A): one pointwise pass
-    // with the partial sums of dW_lin and db
-    CK(launch_pointwise_bwd_saved(x, reinterpret_cast<const float*>(base + LT.gp), dz, da, part,
-                                  epilogue_max_grid(), d.B, d.Ng, (int)d.Ci, (int)d.Co, &rows, s));
+    const float* gp = reinterpret_cast<const float*>(base + LT.gp);
+    if (is_tc(precision) && da_tz_supported(d, nullptr, 0)) {
+      // dA = dz GELU'(A) with the partial sums of dW_lin and db and the t, z
+      // DFT of dA, in one pass over x, dz and GELU'(A)
+      CK(launch_da_tz(x, gp, dz, da, t1, part, epilogue_max_grid(), d, T.Fta, T.Fz, is_split(precision),
+                      precision == FNO_TF32, err, &rows, s));
+      tz_done = true;
+    } else {
+      // dA = dz GELU'(A) from the training forward's GELU'(A): one pointwise
+      // pass with the partial sums of dW_lin and db
+      CK(launch_pointwise_bwd_saved(x, gp, dz, da, part, epilogue_max_grid(), d.B, d.Ng, (int)d.Ci, (int)d.Co,
+                                    &rows, s));
+    }
   } else {
   // dA = dz GELU'(A) with the partial sums of dW_lin and db
   EpiArgs a{};
@@ -612,7 +629,11 @@ static int block_bwd_impl(const fno_dims* dims, int precision, const float* x, c
   }
   CK(launch_reduce_partials(part, rows, (int)d.Ci, (int)d.Co, dw_lin, db, s));
   // G = (c/N) DFT(dA); dW and the input-spectrum gradient
-  if ((rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s, precision, err))) return rc;
+  if (tz_done)
+    rc = spectrum_yx(d, d.Co, T, t1, t2, yh, s, precision);
+  else
+    rc = spectrum_f32(d, d.Co, da, T.Fta, T, t1, t2, yh, s, precision, err);
+  if (rc) return rc;
   CK(launch_mix_adjoint_f32(d, xh, wc, yh, reinterpret_cast<float2*>(dw), gxh, s));
   // dX = inverse(GXh) + W_lin dA
   if ((rc = inverse_xy_f32(d, d.Ci, gxh, T, t2, t1, s, precision))) return rc;

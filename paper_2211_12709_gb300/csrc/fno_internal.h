@@ -144,6 +144,16 @@ cudaError_t launch_fwd_tz_mma(const float* in, float2* out, int64_t ncol, const 
                               const float2* ft, const float2* fz, bool split, bool tf32, int* err,
                               cudaStream_t s);
 
+// The dA pass of a block backward after a training forward fused with the
+// forward pruned t, z DFT of dA (fno_da_tz.cu, mma.sync): writes da, the
+// spectrum t1 = [B Co Nx Ny][Jz][Jt] (ft = Fta) and at most max_rows partial
+// rows of (dW_lin, db) (*rows_out, as launch_pointwise_bwd_saved).  err: device
+// word set to nonzero when a bounded wait gives up.
+bool da_tz_supported(const Dims& d, char* why, size_t nwhy);
+cudaError_t launch_da_tz(const float* x, const float* g, const float* dz, float* da, float2* t1, float* part,
+                         int max_rows, const Dims& d, const float2* ft, const float2* fz, bool split, bool tf32,
+                         int* err, int* rows_out, cudaStream_t s);
+
 #ifdef __CUDACC__
 // Launch with the profiling hooks; returns the launch error from the caller.
 #define FNO_LAUNCH(name, kern, grid, block, smem, stream, ...)   \

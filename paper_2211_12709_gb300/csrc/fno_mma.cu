@@ -42,6 +42,7 @@
 #include <cstdio>
 
 #include "fno_internal.h"
+#include "warp_mma.h"
 #include "tma.h"
 
 namespace fno {
@@ -120,13 +121,10 @@ __device__ __forceinline__ void stsm_x2_t(uint32_t a, uint32_t r0, uint32_t r1) 
                : "memory");
 }
 
-// Round to TF32 (10 stored mantissa bits, nearest, ties away).  A TF32 value is
-// exact as BF16 hi + lo, so split products of rounded operands are TF32 products.
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t y;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-  return __uint_as_float(y);
-}
+// Round to TF32 (nearest, ties away from zero; see warp_mma.h).  A TF32 value
+// is exact as BF16 hi + lo, so split products of rounded operands are TF32
+// products.
+__device__ __forceinline__ float tf32_round(float x) { return wm::tf32_round(x); }
 template <bool TF>
 __device__ __forceinline__ float rnd(float x) {
   return TF ? tf32_round(x) : x;
@@ -884,10 +882,10 @@ static cudaError_t launch_mma_m(const EpiM& k, bool split, bool tf32, int* g, cu
   return split ? launch_mma_t<MODE, true, false>(k, g, s) : launch_mma_t<MODE, false, false>(k, g, s);
 }
 
-// Tensor map of a [rows][chan] FP32 array with boxes of box_rows x 128 points,
-// encoded through the driver entry point (no link-time driver dependency).
-cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long chan, long long rows,
-                         int box_rows) {
+// Tiled tensor map of an FP32 array, encoded through the driver entry point
+// (no link-time driver dependency).  strides: bytes of dimensions 1 .. rank-1.
+cudaError_t encode_tiled(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                         const cuuint64_t* strides, const cuuint32_t* box, bool swizzle128) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                 CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -902,14 +900,21 @@ cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long chan, lo
       return cudaErrorNotSupported;
     fn = reinterpret_cast<EncodeFn>(p);
   }
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tensor map of a [rows][chan] FP32 array with boxes of box_rows x 128 points.
+cudaError_t encode_x_map(CUtensorMap* map, const float* base, long long chan, long long rows,
+                         int box_rows) {
   const cuuint64_t dims[2] = {(cuuint64_t)chan, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)chan * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)kP, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
-                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+  return encode_tiled(map, base, 2, dims, strides, box, false);
 }
 
 cudaError_t launch_epilogue_mma(const Dims& d, const EpiArgs& a, bool split, bool tf32, void* table,

@@ -43,6 +43,7 @@
 #include <algorithm>
 
 #include "fno_internal.h"
+#include "warp_mma.h"
 
 namespace fno {
 
@@ -471,10 +472,10 @@ __global__ void __launch_bounds__(kPwThreads, KB == 1 ? 4 : 1) k_pw_bwd(const Pw
 constexpr int kDaMT = 2;  // m-tiles of 16 over the C_in + 1 rows
 constexpr int kDaNT = 3;  // n-tiles of 8 over the C_out columns
 
+// a = big + small, both rounded to TF32 (nearest, ties away from zero; see
+// warp_mma.h)
 __device__ __forceinline__ void tf32_split(float a, uint32_t& big, uint32_t& small) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(big) : "f"(a));
-  const float r = a - __uint_as_float(big);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(small) : "f"(r));
+  wm::tf32_split(a, big, small);
 }
 // D += A (16x8, row) * B (8x8, col), TF32 in, FP32 accumulate
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,

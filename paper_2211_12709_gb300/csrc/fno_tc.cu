@@ -55,6 +55,7 @@
 #include "fno_internal.h"
 #include "tma.h"
 #include "umma.h"
+#include "warp_mma.h"
 
 namespace fno {
 
@@ -72,11 +73,8 @@ constexpr int kConvWarps = 4;
 constexpr int kTcThreads = 32 * (kWConv + kConvWarps + 8);
 constexpr long long kTcWait = 4000000000LL;  // about 2 s of SM clocks per wait
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t y;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-  return __uint_as_float(y);
-}
+// TF32 rounding (nearest, ties away from zero; see warp_mma.h)
+__device__ __forceinline__ float tf32_rna(float x) { return wm::tf32_round(x); }
 template <bool TF>
 __device__ __forceinline__ float rnd_tf(float x) {
   return TF ? tf32_rna(x) : x;

@@ -78,6 +78,11 @@ TRAIN_CASES = [
     # 32 channels: the tensor-core precisions keep the tensor-core dA epilogue
     # (no GELU'(A) stored), FP32 takes the FP32 dA pass
     (Dims(1, 32, 32, 4, 4, 16, 16, 2, 2, 4, 6), "32 channels: dA epilogue in the tensor-core precisions"),
+    # the fused dA + t,z pass: 31 -> 24 channels and 32 kept z modes (its limits),
+    # 312 columns over at most 152 CTAs, Nt = 16 (two 8-plane n-tiles per chunk)
+    (Dims(2, 31, 24, 12, 13, 32, 16, 3, 3, 16, 8), "31 -> 24 channels, Jz = 32: fused dA + t,z at its limits"),
+    # Nt = 32: a 16-plane z k-step spans two chunks; eight chunks per column
+    (Dims(1, 20, 20, 16, 10, 64, 32, 4, 4, 8, 8), "width 20, 64 x 32 columns: fused dA + t,z over 8 chunks"),
 ]
 
 
