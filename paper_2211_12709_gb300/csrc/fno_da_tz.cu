@@ -17,19 +17,21 @@
 // first and is not used (it is read again, usually from L2, with that chunk).
 //
 // Sixteen warps in two roles, handing each chunk over through mbarriers:
-//   warps 0-7 ("dA warps"), warp w: dA at the points 32 w .. 32 w + 31 for
-//     every output channel, in place of dz in the ring and to global memory;
-//     then its share of (dW_lin, db), the 32 points of block w, on mma.sync
-//     m16n8k8 TF32 with split operands (big.big + big.small + small.big, as
-//     accurate as FP32 products), per chunk from zero, Kahan-folded;
-//   warps 8-15 ("DFT warps"), warp 8 + v, once the chunk's dA is in place:
-//     the t stage of channels o = v, v + 8, v + 16 on mma.sync m16n8k16,
-//     whose accumulators of two 8-plane n-tiles form the B fragment of one
-//     16-plane z k-step; the z stage's totals stay in registers over the
-//     column's chunks and are written at its end ([col][Jz][Jt] complex, the
-//     layout of the separate t, z kernel, with the same products in the same
-//     order).  Lane 0 of warp 8 also keeps the S-stage ring of TMA copies in
-//     flight.
+//   warps 8-15 ("DFT warps"), warp 8 + v: dA at the points 32 v .. 32 v + 31
+//     for every output channel, in place of dz in the ring and to global
+//     memory; then, after a barrier of these warps, the t stage of channels
+//     o = v, v + 8, v + 16 on mma.sync m16n8k16, whose accumulators of two
+//     8-plane n-tiles form the B fragment of one 16-plane z k-step; the z
+//     stage's totals stay in registers over the column's chunks and are
+//     written at its end ([col][Jz][Jt] complex, the layout of the separate
+//     t, z kernel, with the same products in the same order).
+//   warps 0-7 ("dW warps"), warp w, once the chunk's dA is in place: its
+//     share of (dW_lin, db), the 32 points of block w, on mma.sync m16n8k8
+//     TF32 with split operands (big.big + big.small + small.big, as accurate
+//     as FP32 products), per chunk from zero, Kahan-folded.
+// Thread 0 starts the copies of the first S chunks; afterwards the warp that
+// finishes a chunk last (a count per slot) starts the copy of the chunk S
+// places later into its slot.
 //
 // Every wait is bounded (about 2 s of SM clocks) and watches a CTA abort flag:
 // a role that gives up raises it and *err, every role leaves its loop, the
@@ -49,8 +51,8 @@ namespace fno {
 
 namespace {
 
-constexpr int kDtWarpsA = 8;                  // dA and (dW_lin, db) warps
-constexpr int kDtWarpsB = 8;                  // t, z DFT warps
+constexpr int kDtWarpsA = 8;                  // (dW_lin, db) warps
+constexpr int kDtWarpsB = 8;                  // dA and t, z DFT warps
 constexpr int kDtThreads = 32 * (kDtWarpsA + kDtWarpsB);
 constexpr int kDtPoints = 256;                // points per chunk (8 blocks of 32)
 constexpr int kDtBoxBlocks = 9;               // blocks per row of a staged box
@@ -109,6 +111,20 @@ __device__ __forceinline__ bool dt_wait_warp(uint64_t* bar, uint32_t parity, vol
 }
 
 __device__ __forceinline__ void bar_a() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// barrier of the DFT warps (named barrier 2) that also ANDs a predicate, so
+// that they take every decision to leave together
+__device__ __forceinline__ bool bar_b_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 2, 256, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
 }  // namespace
 
 template <bool SPLIT, bool TF, int MZ>
@@ -126,8 +142,9 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
   uint4* fzf = reinterpret_cast<uint4*>(sm + p.o_fz);  // [MZ][KZ][4 parts][32 lanes]
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + p.o_bar);  // [S] the chunk has landed
   uint64_t* dav = full + S;                                     // [S] its dA is in place
-  uint64_t* empty = dav + S;                                    // [S] every warp is done with it
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  int* left = reinterpret_cast<int*>(dav + S);                  // [S] warps not done with the chunk
+  volatile int* abort_flag = left + S;
+  int* s_issued = left + S + 1;                                 // chunks issued so far
   auto raise = [&]() {
     *abort_flag = 1;
     atomicExch(p.err, 1);
@@ -159,9 +176,10 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
     for (int s = 0; s < S; ++s) {
       tma::mbar_init(&full[s], 1);
       tma::mbar_init(&dav[s], kDtWarpsA);
-      tma::mbar_init(&empty[s], kDtWarpsA + kDtWarpsB);
+      left[s] = kDtWarpsA + kDtWarpsB;
     }
     *abort_flag = 0;
+    *s_issued = 0;
     tma::fence_mbar_init();
   }
   __syncthreads();
@@ -194,9 +212,8 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
       }
     }
   };
-  // the producer (lane 0 of warp 8): chunk g into slot g % S
-  const bool producer = (warp == kDtWarpsA && lane == 0);
-  long long issued = 0;
+  // Chunk g goes into slot g % S: the first S chunks now, by thread 0; chunk
+  // g + S by the warp that finishes chunk g last (release_slot).
   auto issue = [&](long long g) {
     const int s = (int)(g % S);
     long long b, xy;
@@ -209,26 +226,35 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
     tma_load_3d(st, &p.mx, blk0, (int)(b * Ci), &full[s]);
     tma_load_3d(st + p.o_dz, &p.mdz, blk0, (int)(b * Co), &full[s]);
     tma_load_3d(st + p.o_gp, &p.mgp, blk0, (int)(b * Co), &full[s]);
-    issued = g + 1;
+    atomicMax(s_issued, (int)(g + 1));
   };
-  if (producer)
+  if (tid == 0)
     for (long long g = 0; g < S && g < nst; ++g) issue(g);
+  // this warp is done with chunk g (slot s): the last of the sixteen refills the slot
+  auto release_slot = [&](long long g, int s) {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicSub(&left[s], 1) == 1) {
+        __threadfence_block();
+        left[s] = kDtWarpsA + kDtWarpsB;
+        if (g + S < nst) issue(g + S);
+      }
+    }
+    __syncwarp();
+  };
 
   if (warp < kDtWarpsA) {
-    // ================= dA warps: dA, then (dW_lin, db) over block w ==========
+    // ================= dW warps: (dW_lin, db) over block w ===================
     const int w = warp;
     const int MT = (Ci + 1 + 15) / 16, NT = (Co + 7) / 8;
     // Per-thread byte offsets in a staged box: every access below is one of
     // eight precomputed offsets plus a compile-time multiple of the row size.
-    //   dA pass: row o, block w, point lane       -> oda[o mod 8] + kDtRow o
     //   x rows g8 + 8 q', block w, points 8 kk + t4 (+4), and dA rows g8 + 8 n
     //   likewise                                  -> ofr[2 kk (+1)] + kDtRow 8 q'
-    uint32_t oda[8], ofr[8];
+    uint32_t ofr[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      oda[j] = swz((uint32_t)j, (uint32_t)w, (uint32_t)lane);
-      ofr[j] = swz((uint32_t)g8, (uint32_t)w, (uint32_t)(4 * j + t4));
-    }
+    for (int j = 0; j < 8; ++j) ofr[j] = swz((uint32_t)g8, (uint32_t)w, (uint32_t)(4 * j + t4));
     float sum[2][3][4], cmp[2][3][4];
 #pragma unroll
     for (int m = 0; m < 2; ++m)
@@ -248,34 +274,17 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
         xone[m][r] = (i == Ci) ? 1.f : 0.f;
       }
     const bool din[3] = {g8 < Co, 8 + g8 < Co, 16 + g8 < Co};
-    Walk cw = walk_start();
     int s = 0;
     uint32_t ph = 0;
-    for (long long g = 0; g < nst; ++g, walk_next(cw), s = (s + 1 == S) ? 0 : s + 1, ph ^= (s == 0)) {
-      if (!dt_wait_warp(&full[s], ph, abort_flag)) {
+    for (long long g = 0; g < nst; ++g, s = (s + 1 == S) ? 0 : s + 1, ph ^= (s == 0)) {
+      // the chunk has landed and the DFT warps have put dA in place of dz
+      if (!dt_wait_warp(&dav[s], ph, abort_flag)) {
         if (lane == 0) raise();
         break;
       }
-      const long long b = cw.b, xy = cw.xy;
-      const int k = cw.k;
       const unsigned char* xs = sm + (size_t)s * p.stage_bytes;
-      unsigned char* ds = sm + (size_t)s * p.stage_bytes + p.o_dz;
-      const unsigned char* gs = sm + (size_t)s * p.stage_bytes + p.o_gp;
-      // 1. dA = dz GELU'(A) at this thread's point, in place and to global memory
-      float* dag = p.da + (b * Co) * p.chan + xy * p.plane + (long long)k * kDtPoints + 32 * w + lane;
-#pragma unroll
-      for (int o = 0; o < kDtWarpsB * kDtCPW; ++o) {
-        if (o < Co) {
-          const uint32_t off = oda[o & 7] + kDtRow * (uint32_t)(o & ~7);
-          float* dp = reinterpret_cast<float*>(ds + off);
-          const float v = *dp * *reinterpret_cast<const float*>(gs + off);
-          *dp = v;
-          dag[(long long)o * p.chan] = v;
-        }
-      }
-      __syncwarp();
-      if (lane == 0) tma::mbar_arrive(&dav[s]);
-      // 2. (dW_lin, db) over the 32 points of block w: rows i of x (row Ci the
+      const unsigned char* ds = sm + (size_t)s * p.stage_bytes + p.o_dz;
+      // (dW_lin, db) over the 32 points of block w: rows i of x (row Ci the
       // ones row of db; rows past it enter as zeros), columns o of dA (columns
       // past Co are zeros and discarded), k = point
       float acc[2][3][4];
@@ -323,8 +332,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
           }
         }
       }
-      __syncwarp();
-      if (lane == 0) tma::mbar_arrive(&empty[s]);  // this warp is done with the chunk
+      release_slot(g, s);
 #pragma unroll
       for (int m = 0; m < 2; ++m)
 #pragma unroll
@@ -338,9 +346,16 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
           }
     }
     // (dW_lin, db) partials: fold[warp][pair] in the ring once every role is
-    // done with it (the barrier below), then a fixed-order sum over the warps
+    // done with it and every copy started has landed, then a fixed-order sum
+    // over the warps
     const int npair = Ci * Co + Co;
     __syncthreads();
+    if (tid == 0) {
+      const long long issued = *s_issued;
+      for (long long q = (issued > S ? issued - S : 0); q < issued; ++q)
+        (void)tma::mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), kDtWait);
+    }
+    bar_a();
     float* fold = reinterpret_cast<float*>(sm);
 #pragma unroll
     for (int m = 0; m < 2; ++m)
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
     return;
   }
 
-  // ================= DFT warps: the t, z DFT of dA ===========================
+  // ================= DFT warps: dA, then the t, z DFT of dA ==================
   const int v = warp - kDtWarpsA;
   // t basis fragments in registers (KT <= 2): rows ri * 8 + jt, k slots
   // 2 t4 + {0,1} <-> t = 16 ks + 4 t4 + {0,1} and 2 t4 + 8 + {0,1} <-> + {2,3}
@@ -397,6 +412,10 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
       const uint32_t pt = (uint32_t)((8 * h + g8) * Nt + 16 * ks + 4 * t4) & 255u;
       otz[h][ks] = swz((uint32_t)v, pt >> 5, pt & 31u);
     }
+  // the dA pass reads row o, block v, point lane: oda[o mod 8] + kDtRow (o - o mod 8)
+  uint32_t oda[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) oda[j] = swz((uint32_t)j, (uint32_t)v, (uint32_t)lane);
   float tre[kDtCPW][MZ][4], tim[kDtCPW][MZ][4];
   uint32_t pend[kDtCPW][4];
 #pragma unroll
@@ -412,13 +431,31 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
   int s = 0;
   uint32_t ph = 0;
   for (long long g = 0; g < nst; ++g, walk_next(cw), s = (s + 1 == S) ? 0 : s + 1, ph ^= (s == 0)) {
-    if (!dt_wait_warp(&dav[s], ph, abort_flag)) {
-      if (lane == 0) raise();
-      break;
-    }
+    bool ok = dt_wait_warp(&full[s], ph, abort_flag);
+    if (!ok && lane == 0) raise();
     const long long b = cw.b, xy = cw.xy;
     const int k = cw.k;
-    const unsigned char* db_ = sm + (size_t)s * p.stage_bytes + p.o_dz;
+    unsigned char* db_ = sm + (size_t)s * p.stage_bytes + p.o_dz;
+    if (ok) {
+      // dA = dz GELU'(A) at the points 32 v .. 32 v + 31, in place and to global memory
+      const unsigned char* gs = sm + (size_t)s * p.stage_bytes + p.o_gp;
+      float* dag = p.da + (b * Co) * p.chan + xy * p.plane + (long long)k * kDtPoints + 32 * v + lane;
+#pragma unroll
+      for (int o = 0; o < kDtWarpsB * kDtCPW; ++o) {
+        if (o < Co) {
+          const uint32_t off = oda[o & 7] + kDtRow * (uint32_t)(o & ~7);
+          float* dp = reinterpret_cast<float*>(db_ + off);
+          const float dv = *dp * *reinterpret_cast<const float*>(gs + off);
+          *dp = dv;
+          dag[(long long)o * p.chan] = dv;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) tma::mbar_arrive(&dav[s]);
+    }
+    // every DFT warp's dA is in place (the t stage reads every block); the
+    // DFT warps take every decision to leave together
+    if (!bar_b_and(ok && *abort_flag == 0)) break;
 #pragma unroll
     for (int j = 0; j < kDtCPW; ++j) {
       const int o = v + kDtWarpsB * j;
@@ -483,16 +520,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
         }
       }
     }
-    __syncwarp();
-    if (lane == 0) tma::mbar_arrive(&empty[s]);  // this warp is done with the chunk
-    if (producer && g + S < nst) {
-      // slot s takes chunk g + S once every warp is done with chunk g
-      if (!dt_wait(&empty[s], ph, abort_flag)) {
-        raise();
-      } else {
-        issue(g + S);
-      }
-    }
+    release_slot(g, s);
     if (k == p.NCK - 1) {
       // the column's spectrum: T[col][kz][jt], rows kz = 16 mt + g8 (+8), cols jt = 2 t4 + {0, 1}
 #pragma unroll
@@ -520,12 +548,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
       }
     }
   }
-  if (producer) {
-    // every copy this thread started has landed before the ring is reused or released
-    for (long long q = (issued > S ? issued - S : 0); q < issued; ++q)
-      (void)tma::mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), kDtWait);
-  }
-  __syncthreads();  // pairs with the dA warps' barrier before their fold
+  __syncthreads();  // pairs with the dW warps' barrier before their fold
 }
 
 // ---------------------------------------------------------------------------
@@ -578,7 +601,7 @@ static bool da_tz_plan(const Dims& d, DaTz& k, size_t& smem, const char** why) {
   for (int S = 4; S >= 2; --S) {
     const uint32_t o_fz = (uint32_t)S * k.stage_bytes;
     const uint32_t o_bar = o_fz + fz_bytes;
-    const size_t total = (size_t)o_bar + 24u * (uint32_t)S + 16u + 1024u;  // + alignment pad
+    const size_t total = (size_t)o_bar + 16u * (uint32_t)S + 4u * (uint32_t)(S + 2) + 1024u;  // + alignment pad
     if (total <= kDtSmemMax) {
       k.S = S;
       k.o_fz = o_fz;
