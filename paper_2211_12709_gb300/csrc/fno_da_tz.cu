@@ -214,22 +214,22 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
   };
   // Chunk g goes into slot g % S: the first S chunks now, by thread 0; chunk
   // g + S by the warp that finishes chunk g last (release_slot).
-  auto issue = [&](long long g) {
-    const int s = (int)(g % S);
-    long long b, xy;
-    int k;
-    chunk_at(g, b, xy, k);
-    const int blk0 = (int)((xy * p.plane + (long long)k * kDtPoints) >> 5);
+  // (32-bit arithmetic: the host keeps chunk and block counts below 2^31)
+  const int cb32 = (int)c_begin, nck = p.NCK, nxny = (int)p.NxNy, bpc = (int)(p.plane >> 5);
+  auto issue = [&](int g, int s) {
+    const int cl = g / nck, k = g - cl * nck, c = cb32 + cl;
+    const int b = c / nxny, xy = c - b * nxny;
+    const int blk0 = xy * bpc + k * (kDtPoints / 32);
     const uint32_t st = sbase + (uint32_t)s * p.stage_bytes;
     tma::fence_proxy_async();
     tma::mbar_arrive_expect_tx(&full[s], p.stage_bytes_tx);
-    tma_load_3d(st, &p.mx, blk0, (int)(b * Ci), &full[s]);
-    tma_load_3d(st + p.o_dz, &p.mdz, blk0, (int)(b * Co), &full[s]);
-    tma_load_3d(st + p.o_gp, &p.mgp, blk0, (int)(b * Co), &full[s]);
-    atomicMax(s_issued, (int)(g + 1));
+    tma_load_3d(st, &p.mx, blk0, b * Ci, &full[s]);
+    tma_load_3d(st + p.o_dz, &p.mdz, blk0, b * Co, &full[s]);
+    tma_load_3d(st + p.o_gp, &p.mgp, blk0, b * Co, &full[s]);
+    atomicMax(s_issued, g + 1);
   };
   if (tid == 0)
-    for (long long g = 0; g < S && g < nst; ++g) issue(g);
+    for (int g = 0; g < S && g < nst; ++g) issue(g, g);
   // this warp is done with chunk g (slot s): the last of the sixteen refills the slot
   auto release_slot = [&](long long g, int s) {
     __syncwarp();
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_da_tz(const __grid_constant__
       if (atomicSub(&left[s], 1) == 1) {
         __threadfence_block();
         left[s] = kDtWarpsA + kDtWarpsB;
-        if (g + S < nst) issue(g + S);
+        if (g + S < nst) issue((int)(g + S), s);
       }
     }
     __syncwarp();
@@ -573,7 +573,9 @@ static bool da_tz_plan(const Dims& d, DaTz& k, size_t& smem, const char** why) {
   else if (d.Jt > 8) r = "more than 8 kept t modes";
   else if (d.Jz > 32) r = "more than 32 kept z modes";
   else if (d.Ci + 1 > 32 || d.Co > kDtWarpsB * kDtCPW) r = "more than 31 input or 24 output channels";
-  else if (d.B * d.Ci > (1 << 30) || d.B * d.Co > (1 << 30) || d.Ng / 32 > (1LL << 30)) r = "sizes too large";
+  else if (d.B * d.Ci > (1 << 30) || d.B * d.Co > (1 << 30) || d.Ng / 32 > (1LL << 30) ||
+           d.B * d.Nx * d.Ny * (d.Nz * d.Nt / kDtPoints) > (1LL << 30))
+    r = "sizes too large";
   if (r) {
     if (why) *why = r;
     return false;
