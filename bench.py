@@ -153,6 +153,8 @@ def algorithmic(name, d):
         return 3 * grid + t1, f_inv + f_lin
     if name.startswith("fno_epi_fwd"):
         return 2 * grid + t1, f_inv + f_lin
+    if name.startswith("fno_da_tz"):  # reads x, dz, GELU'(A); writes dA and its t,z spectrum
+        return 4 * grid + t1, f_lin + f_tz
     if name.startswith("fno_da_saved"):  # reads x, dz, GELU'(A); writes dA
         return 4 * grid, f_lin
     if name.startswith("fno_epi_da"):
@@ -178,11 +180,11 @@ TRAFFIC_PER_UNIT = {
     "fno_epi_dx_f32": (0.804837e9 + 0.609467e9) / 167772160,
     "fno_epi_da_mma_bf16x3": (1.471207e9 + 0.646687e9) / 167772160,
     "fno_epi_fwd_train_mma_bf16x3": (0.801008e9 + 1.291166e9) / 167772160,
-    "fno_da_saved": (2.013355e9 + 0.647265e9) / 167772160,
     "fno_epi_dx_mma_bf16x3": (0.800973e9 + 0.613033e9) / 167772160,
-    "fno_fwd_tz_mma_bf16x3": (0.671163e9 + 0.112208e9) / 167772160,
-    "fno_epi_fwd_train_tc_bf16x3": (0.798249e9 + 1.285758e9) / 167772160,
-    "fno_epi_dx_tc_bf16x3": (0.798222e9 + 0.608979e9) / 167772160,
+    "fno_fwd_tz_mma_bf16x3": (0.671138e9 + 0.108852e9) / 167772160,
+    "fno_epi_fwd_train_tc_bf16x3": (0.798273e9 + 1.285392e9) / 167772160,
+    "fno_epi_dx_tc_bf16x3": (0.798813e9 + 0.609447e9) / 167772160,
+    "fno_da_tz_bf16x3": (2.016318e9 + 0.765664e9) / 167772160,
 }
 
 
@@ -200,7 +202,7 @@ def roofline_of(name, per_launch_ms, dd, pk, precision):
     gbs = nbytes / sec / 1e9
     tfl = nflops / sec / 1e12
     f_hbm = gbs / pk["hbm_gbs"]
-    if "_tc_" in name or "_mma_" in name:
+    if "_tc_" in name or "_mma_" in name or name.startswith("fno_da_tz"):
         # tensor-core kernels (mma.sync): algorithmic flops against
         # the dense BF16 peak; split BF16 issues 3 (DFT stages) or 6 (1x1
         # stages) products per real multiply-add, which the fraction leaves out
@@ -738,6 +740,8 @@ def main():
     e1.record(stream)
     barrier()
     prof = _lib.fno_profile_stop()
+    # a bounded device-side wait that gave up would void the timing: raise
+    _lib.fno_workspace_status(ws.data_ptr(), sh)
     launches = _lib.fno_launch_count() - n0
     clocks = sampler.stop()
     ms = reduce_step_time(e0.elapsed_time(e1) / args.steps, dist, dev)

@@ -37,6 +37,7 @@ def test_traffic_entries_name_launches_of_the_library():
     b = _bench()
     names = launch_names()
     assert "fno_da_saved" in names and "fno_epi_fwd_train_mma_bf16x3" in names
+    assert "fno_da_tz_bf16x3" in names
     for key in b.TRAFFIC_PER_UNIT:
         assert key in names, key
 
@@ -45,7 +46,7 @@ def test_every_heavy_launch_has_algorithmic_bytes():
     b = _bench()
     heavy = [n for n in launch_names()
              if n.startswith(("fno_epi_fwd", "fno_epi_da", "fno_epi_dx", "fno_fwd_tz", "fno_da_saved",
-                              "fno_mix"))]
+                              "fno_da_tz", "fno_mix"))]
     assert len(heavy) >= 20
     for n in heavy:
         nbytes, _ = b.algorithmic(n, DD)
@@ -59,16 +60,22 @@ def test_training_forward_counts_the_derivative_store():
     train, _ = b.algorithmic("fno_epi_fwd_train_mma_bf16x3", DD)
     plain, _ = b.algorithmic("fno_epi_fwd_mma_bf16x3", DD)
     assert train - plain == GRID
-    # the dA pass reads x, dz and GELU'(A) and writes dA
+    # the dA pass reads x, dz and GELU'(A) and writes dA; the fused pass also
+    # writes the t,z spectrum of dA and adds the t,z DFT's flops
     assert b.algorithmic("fno_da_saved", DD)[0] == 4 * GRID
+    fb, ff = b.algorithmic("fno_da_tz_bf16x3", DD)
+    tb, tf = b.algorithmic("fno_fwd_tz_mma_bf16x3", DD)
+    assert fb == 4 * GRID + (tb - GRID)
+    assert ff == b.algorithmic("fno_da_saved", DD)[1] + tf
 
 
 def test_roofline_fraction_is_algorithmic_bytes_over_time_over_peak():
     b = _bench()
     pk = {"hbm_gbs": 6754.1, "bf16_tflops": 1929.9, "sm_max_mhz": 2070.0, "src": "measured"}
-    r = b.roofline_of("fno_da_saved", 4.94, DD, pk, "bf16x3")
-    achieved = 4 * GRID / 4.94e-3 / 1e9
+    nbytes = b.algorithmic("fno_da_tz_bf16x3", DD)[0]
+    r = b.roofline_of("fno_da_tz_bf16x3", 4.81, DD, pk, "bf16x3")
+    achieved = nbytes / 4.81e-3 / 1e9
     assert r["bound"] == "hbm"
     assert abs(r["achieved"] - achieved) < 0.5
     assert abs(r["frac"] - achieved / 6754.1) < 1e-3
-    assert r["traffic"] is not None and abs(r["traffic"] / (4 * GRID) - 1) < 0.05
+    assert r["traffic"] is not None and abs(r["traffic"] / nbytes - 1) < 0.05
