@@ -269,9 +269,10 @@ def errors_vs_oracle(ref, outs, pts):
     return out
 
 
-def precision_sweep(args, step_of, outs, stream, barrier, units, ref=None, pts=None):
+def precision_sweep(args, step_of, outs, stream, barrier, units, ref=None, pts=None, check=None):
     """Time every precision on the resident inputs; rel-L2 of every result against
-    the FP64 oracle (ref, at the sampled points pts) and against the FP32 plain form."""
+    the FP64 oracle (ref, at the sampled points pts) and against the FP32 plain form.
+    check() raises if a bounded device-side wait of the timed steps gave up."""
     import torch
     ref_prec = "fp32"
     runs = {}
@@ -288,6 +289,8 @@ def precision_sweep(args, step_of, outs, stream, barrier, units, ref=None, pts=N
             st()
         b.record(stream)
         barrier()
+        if check is not None:
+            check()
         ms = a.elapsed_time(b) / args.steps
         res = [t.detach().double().clone() if prec == ref_prec else t.detach().double() for t in outs]
         if prec == ref_prec:
@@ -613,7 +616,7 @@ def shape_sweep(name, args, dev, stream, barrier, cfg):
     pts = sample_points((Nx, Ny, Nz, Nt), 96, 78)
     ref = oracle_reference(Dims(B, C, C, Nx, Ny, Nz, Nt, mx, my, mz, mt), x_np, w_np, wl_np, b_np, dz_np, pts)
     out = precision_sweep(args, step_of, (z, dx, dw, dwl, db), stream, barrier, B * C * Nx * Ny * Nz * Nt,
-                          ref, pts)
+                          ref, pts, check=lambda: _lib.fno_workspace_status(ws.data_ptr(), sh))
     out["config"] = {"B": B, "C_in": C, "C_out": C, "grid": [Nx, Ny, Nz, Nt], "modes": [mx, my, mz, mt]}
     del x, dz, z, dx, ws
     return out
@@ -847,7 +850,7 @@ def main():
         pts = sample_points((Nx, Ny, Nz, Nt), 96, 77)
         ref = oracle_reference(od, x_h.numpy(), w_np, wl_np, b_np, dz_h.numpy(), pts)
         sweep = precision_sweep(args, step_of, (z, dx, dw, dwl, db), stream, barrier, units * world,
-                                ref, pts)
+                                ref, pts, check=lambda: _lib.fno_workspace_status(ws.data_ptr(), sh))
         if args.workload != SMALL_WORKLOAD:
             sweep[SMALL_WORKLOAD] = shape_sweep(SMALL_WORKLOAD, args, dev, stream, barrier, cfg)
 
