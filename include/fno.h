@@ -159,8 +159,11 @@ int fno_block_bwd(const fno_dims* dims, int precision, const float* x, const flo
  * there and runs only the adjoint chain, computing what fno_block_bwd
  * computes.  After fno_block_fwd_train it also takes GELU'(A) from there:
  * dA, dw_lin and db then come from one pointwise pass over x, dz and GELU'(A)
- * (FP32 products, Kahan-summed), and agree with fno_block_bwd to rounding
- * rather than bitwise.
+ * (FP32-accurate products, Kahan-summed), and agree with fno_block_bwd to
+ * rounding rather than bitwise.  In the tensor-core precisions, for Nt = 16 or
+ * 32, Nz a multiple of 16, mt <= 8, 2 mz <= 32, C_in <= 31 and C_out <= 24,
+ * that pass also forms the t, z DFT of dA (the first stages of the dw and dx
+ * spectra), so dA is written once and not read back for them.
  * Contract: ws (and ws_bytes, sized for FNO_OP_BLOCK_BWD after fno_block_fwd,
  * FNO_OP_BLOCK_TRAIN after fno_block_fwd_train) is the workspace of the last
  * forward call made with it, with the same dims, precision, x and w, and no
