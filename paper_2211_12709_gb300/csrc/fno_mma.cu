@@ -960,8 +960,10 @@ namespace fno {
 //   A[(q,1)][(n,1)] = Re T;  B[(n, part)][i] = part of in[o][n][i].
 // A B-fragment slot pair (2 t4, 2 t4 + 1) is exactly one input float2.  Each
 // warp computes 16 columns of one o; with few m-tiles (M <= 64) it streams K,
-// otherwise it holds all of K for its columns and walks the m-tiles.  Split
-// BF16 uses three-way splits of both operands (six products), BF16 one product.
+// otherwise it holds all of K for its columns and walks the m-tiles.  Its
+// loads run one k-step (streaming) or one task (walk) ahead of the products,
+// so that their latency overlaps tensor-core work.  Split BF16 uses three-way
+// splits of both operands (six products), BF16 one product.
 // ---------------------------------------------------------------------------
 struct LineM {
   const float2* in;
@@ -1009,21 +1011,42 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
 
   const long long ntask = L.outer * L.ncb;
   const long long nw = (long long)gridDim.x * 8;
+  // B inputs of k-step ks for the 16 columns from i0 (rows n = 8 ks + 4 hf + t4 of src)
+  auto loadRaw = [&](const float2* src, long long i0, int ks, float2 (&vr)[2][2]) {
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const long long col = i0 + 8 * nt + g8;
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int n = 8 * ks + 4 * hf + t4;
+        vr[nt][hf] = make_float2(0.f, 0.f);
+        if (n < nin && col < L.inner) vr[nt][hf] = __ldg(src + (size_t)n * L.inner + col);
+      }
+    }
+  };
+  // every k-step's inputs of task tk (the m-tile walk holds them all)
+  auto loadTask = [&](long long tk, float2 (&v)[kLineKSMax][2][2]) {
+    const long long o = tk / L.ncb;
+    const float2* src = L.in + (size_t)o * nin * L.inner;
+#pragma unroll
+    for (int ks = 0; ks < kLineKSMax; ++ks)
+      if (ks < KS) loadRaw(src, (tk - o * L.ncb) * 16, ks, v[ks]);
+  };
+  // m-tile walk: the next task's inputs are in flight while this task's products run
+  float2 vnx[kLineKSMax][2][2];
+  if (!KOUTER && (long long)blockIdx.x * 8 + warp < ntask) loadTask((long long)blockIdx.x * 8 + warp, vnx);
   for (long long task = (long long)blockIdx.x * 8 + warp; task < ntask; task += nw) {
     const long long o = task / L.ncb;
     const long long i0 = (task - o * L.ncb) * 16;
     const float2* src = L.in + (size_t)o * nin * L.inner;
     float2* dst = L.out + (size_t)o * nout * L.inner;
-    // B fragments of k-step ks for the two n-tiles of this warp's 16 columns
-    auto loadB = [&](int ks, uint32_t (&bh)[2][2], uint32_t (&bm)[2][2], uint32_t (&bl)[2][2]) {
+    // B fragments (split parts) of one k-step for the two n-tiles of this warp's 16 columns
+    auto convB = [&](const float2 (&vr)[2][2], uint32_t (&bh)[2][2], uint32_t (&bm)[2][2], uint32_t (&bl)[2][2]) {
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
-        const long long col = i0 + 8 * nt + g8;
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
-          const int n = 8 * ks + 4 * hf + t4;
-          float2 v = make_float2(0.f, 0.f);
-          if (n < nin && col < L.inner) v = __ldg(src + (size_t)n * L.inner + col);
+          float2 v = vr[nt][hf];
           v.x = rnd<TF>(v.x);
           v.y = rnd<TF>(v.y);
           if (SPLIT)
@@ -1074,10 +1097,14 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
       // the tensor-core FP32 accumulation is not round-to-nearest, so each
-      // k-step accumulates from zero and is added into the total in FP32
+      // k-step accumulates from zero and is added into the total in FP32; the
+      // next k-step's inputs are loaded before this k-step's products
+      float2 vr[2][2];
+      loadRaw(src, i0, 0, vr);
       for (int ks = 0; ks < KS; ++ks) {
         uint32_t bh[2][2], bm[2][2], bl[2][2];
-        loadB(ks, bh, bm, bl);
+        convB(vr, bh, bm, bl);
+        if (ks + 1 < KS) loadRaw(src, i0, ks + 1, vr);
 #pragma unroll
         for (int mt = 0; mt < kLineMTMax; ++mt)
           if (mt < MT) {
@@ -1101,7 +1128,8 @@ __global__ void __launch_bounds__(256) k_line_mma(const LineM L) {
       uint32_t bh[kLineKSMax][2][2], bm[kLineKSMax][2][2], bl[kLineKSMax][2][2];
 #pragma unroll
       for (int ks = 0; ks < kLineKSMax; ++ks)
-        if (ks < KS) loadB(ks, bh[ks], bm[ks], bl[ks]);
+        if (ks < KS) convB(vnx[ks], bh[ks], bm[ks], bl[ks]);
+      if (task + nw < ntask) loadTask(task + nw, vnx);
       for (int mt = 0; mt < MT; ++mt) {
         float acc[2][4];
 #pragma unroll
