@@ -172,9 +172,29 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t err;  // device status word (nonzero: a bounded wait gave up)
   size_t tab[10];
-  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, tc_tab, gp, total;
+  size_t t1, t2, xh, yh, gxh, da, part, mma_tab, tc_tab, gp, vz, total;  // vz 0: no region
   bool da_in_dx;
 };
+
+// Grids that the fused epilogues do not tile (Nt other than 16 and 32, or
+// their other limits) take the synthesis path in the tensor-core precisions:
+// the inverse z stage as a tensor-core line into V = [B Cs Nx Ny][Nz][Jt],
+// the inverse t stage to real points (launch_synth_t) straight into the
+// output, and the 1x1, bias and GELU in place (launch_pw_add).
+static bool synth_shape_ok(const Dims& d, int64_t Cs, int64_t Cl) {
+  return synth_t_supported((int)d.Nt, (int)d.Jt) && line_mma_supported((int)d.Jz, (int)d.Nz) &&
+         Cs >= 1 && Cs <= 32 && (Cl == 0 || pw_add_supported((int)Cl, (int)Cs));
+}
+// whether a workspace for these sizes holds V: some epilogue mode of the block
+// or the spectral convolution is then outside the mma.sync epilogue's tiling
+static bool synth_region(const Dims& d) {
+  const int Ci = (int)d.Ci, Co = (int)d.Co;
+  if (!synth_shape_ok(d, Co, Ci) || !synth_shape_ok(d, Ci, Co)) return false;
+  return !(epilogue_mma_supported(d, EPI_FWD, Co, Ci, nullptr, 0) &&
+           epilogue_mma_supported(d, EPI_DX, Ci, Co, nullptr, 0) &&
+           epilogue_mma_supported(d, EPI_SPECTRAL, Co, 0, nullptr, 0) &&
+           epilogue_mma_supported(d, EPI_SPECTRAL, Ci, 0, nullptr, 0));
+}
 
 static Layout layout(const Dims& d, int op) {
   Layout L{};
@@ -221,6 +241,11 @@ static Layout layout(const Dims& d, int op) {
   if (op == FNO_OP_BLOCK_TRAIN) {
     L.gp = off;  // GELU'(A) of the training forward, [B][C_out][grid]
     off += align256(sizeof(float) * (size_t)(d.B * d.Co * d.Ng));
+  }
+  if (synth_region(d)) {
+    const int64_t Cm2 = d.Ci > d.Co ? d.Ci : d.Co;
+    L.vz = off;  // inverse z stage of the synthesis path, [B Cm Nx Ny][Nz][Jt]
+    off += align256(sizeof(float2) * (size_t)(d.B * Cm2 * d.Nx * d.Ny * d.Nz * d.Jt));
   }
   L.total = off;
   return L;
@@ -294,6 +319,30 @@ static int inverse_xy_f32(const Dims& d, int64_t C, const float2* sp, const Tabl
   return FNO_OK;
 }
 
+// The synthesis path (see synth_shape_ok): the dX form writes its 1x1 term
+// first, while dA (which may live in dx) is intact, and the inverse t stage
+// adds to it; the forward writes S into z first and the pointwise pass reads
+// it back as the summand of A.
+static cudaError_t synth_epilogue(const Dims& d, const EpiArgs& a, int precision, float2* V,
+                                  cudaStream_t s) {
+  const int64_t cols = d.B * a.Cs * d.Nx * d.Ny;
+  const bool dx = (a.mode == EPI_DX);
+  if (dx) {
+    cudaError_t e = launch_pw_add(a.lin_in, a.wlin, a.w_si, a.w_sc, nullptr, a.out, nullptr, d.B, d.Ng,
+                                  a.Cl, a.Cs, false, s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = line(a.U, V, cols, (int)d.Jz, (int)d.Nz, d.Jt, a.Iz, precision, s);
+  if (e != cudaSuccess) return e;
+  e = launch_synth_t(V, a.out, cols * d.Nz, (int)d.Nt, (int)d.Jt, a.It, dx, is_split(precision),
+                     precision == FNO_TF32, s);
+  if (e != cudaSuccess) return e;
+  if (a.mode == EPI_FWD)
+    return launch_pw_add(a.lin_in, a.wlin, a.w_si, a.w_sc, a.bias, a.out, a.gp, d.B, d.Ng, a.Cl, a.Cs, true,
+                         s);
+  return cudaSuccess;
+}
+
 // The fused inverse z, t + epilogue stage: split BF16 and TF32 on tcgen05 (TMEM
 // accumulators) where its tiling applies, then warp-level mma.sync (plain BF16,
 // the dA mode and the shapes tcgen05 does not tile), else FP32 on the CUDA
@@ -307,6 +356,8 @@ static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base,
   if (is_tc(precision) && epilogue_mma_supported(d, a.mode, a.Cs, a.Cl, nullptr, 0))
     return launch_epilogue_mma(d, a, is_split(precision), precision == FNO_TF32, base + L.mma_tab, err,
                                grid_used, s);
+  if (is_tc(precision) && a.mode != EPI_DA && L.vz != 0 && synth_shape_ok(d, a.Cs, a.Cl))
+    return synth_epilogue(d, a, precision, reinterpret_cast<float2*>(base + L.vz), s);
   return launch_epilogue_f32(d, a, grid_used, s);
 }
 

@@ -108,6 +108,13 @@ cudaError_t launch_epilogue_tc(const Dims& d, const EpiArgs& a, bool split, bool
 bool line_mma_supported(int nin, int nout);
 cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int nin, int nout,
                             int64_t inner, const float2* tab, bool split, bool tf32, cudaStream_t s);
+// The inverse t stage to real points on mma.sync (fno_mma.cu), for grids the
+// fused epilogues do not tile: out[r][t] (+)= sum_jt Re(It[jt][t] V[r][jt]),
+// r < R, t < Nt <= 128, Jt <= 8; accumulate adds to out instead of writing it.
+// Precisions as launch_line_mma.
+bool synth_t_supported(int Nt, int Jt);
+cudaError_t launch_synth_t(const float2* V, float* out, int64_t R, int Nt, int Jt, const float2* It,
+                           bool accumulate, bool split, bool tf32, cudaStream_t s);
 
 // ---- layers around the blocks (fno_pointwise.cu) ---------------------------
 // y[b,o,p] = act(sum_i x[b,i,p] w[i,o] + bias[o]) (bias nullable, act 0/1 = none/GELU).
@@ -119,6 +126,13 @@ cudaError_t launch_pointwise_bwd(const float* x, const float* w, const float* bi
                                  const float* dy, float* dx, float* part, int64_t B, int64_t P,
                                  int Ci, int Co, int act, int* rows_out, cudaStream_t s);
 size_t pointwise_smem_bytes(int Ci, int Co, bool saved_grad = false);
+// The block's 1x1 + bias + GELU in place around a synthesised spectral part
+// (grids the fused epilogues do not tile): fwd out = GELU(out + bias + W x),
+// gp = GELU'(same) (nullable); else out = W x (x may be out).  W(i, c) =
+// w[i w_si + c w_sc]; Cl, Cs <= 32.
+bool pw_add_supported(int Cl, int Cs);
+cudaError_t launch_pw_add(const float* x, const float* w, int w_si, int w_sc, const float* bias, float* out,
+                          float* gp, int64_t B, int64_t P, int Cl, int Cs, bool fwd, cudaStream_t s);
 int pointwise_max_grid(int Ci, int Co);  // the most rows launch_pointwise_bwd writes
 // The dA step of a block backward after a training forward: dA = dz * g (g the
 // forward's GELU'(A)), written to da, with the (dW_lin, db) partial sums of

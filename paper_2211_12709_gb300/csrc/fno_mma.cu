@@ -1204,6 +1204,186 @@ cudaError_t launch_line_mma(const float2* in, float2* out, int64_t outer, int ni
                 : launch_line_t<false, false, false>(L, smem, "fno_line_mma_bf16", s);
 }
 
+// ---------------------------------------------------------------------------
+// Inverse t stage to real points on the tensor cores, for grids whose Nt the
+// fused epilogues do not tile (Nt other than 16 and 32, e.g. the paper's 84
+// and 86):
+//   S[r][t] = sum_jt Re(It[jt][t] V[r][jt])        r = (column, z), t < Nt
+// with It carrying c(kt)/N.  As a real GEMM over K = 16 = (jt, re/im):
+//   A[r][(jt, 0)] = Re V, A[r][(jt, 1)] = Im V   (one float2 of V fills one
+//   A-fragment slot pair), B[(jt, 0)][t] = Re It, B[(jt, 1)][t] = -Im It.
+// A warp owns 16 rows at a time, loads the next 16 before this one's products
+// and walks the n-tiles of 8 t into a shared-memory tile of its own; the 16
+// rows are one contiguous run of out, which the warp then writes (or adds to:
+// the dX form, whose 1x1 term is written first) with 16-byte accesses.  Split
+// BF16 and TF32 take three-way splits of both operands (six products), BF16 one.
+// ---------------------------------------------------------------------------
+struct SynthT {
+  const float2* V;   // [R][Jt]
+  const float2* It;  // [Jt][Nt]
+  float* out;        // [R][Nt]
+  long long R;
+  int Nt, Jt, NTN, accumulate;
+};
+
+constexpr int kSynthNTMax = 16;  // n-tiles of 8 t (Nt <= 128)
+
+template <bool SPLIT, bool TF>
+__global__ void __launch_bounds__(256) k_synth_t(const SynthT k) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int NP = SPLIT ? 3 : 1;
+  uint2* bfr = reinterpret_cast<uint2*>(smem);  // [NTN][NP][32 lanes]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int Nt = k.Nt, Jt = k.Jt;
+
+  // B fragments of the t basis: b0 = (k 2 t4, 2 t4 + 1; n g8) = jt t4,
+  // b1 = the same at jt t4 + 4; n = t
+  for (int e = tid; e < k.NTN * 32; e += 256) {
+    const int nt = e >> 5, ln = e & 31;
+    const int t = 8 * nt + (ln >> 2);
+    uint32_t h[2], m[2], l[2];
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int jt = (ln & 3) + 4 * hf;
+      float re = 0.f, im = 0.f;
+      if (jt < Jt && t < Nt) {
+        const float2 f = k.It[(size_t)jt * Nt + t];
+        re = rnd<TF>(f.x);
+        im = rnd<TF>(-f.y);
+      }
+      if (SPLIT)
+        split3(re, im, h[hf], m[hf], l[hf]);
+      else
+        split2(re, im, h[hf], l[hf]);
+    }
+    uint2* dst = bfr + (size_t)nt * NP * 32 + ln;
+    dst[0] = make_uint2(h[0], h[1]);
+    if (SPLIT) {
+      dst[32] = make_uint2(m[0], m[1]);
+      dst[64] = make_uint2(l[0], l[1]);
+    }
+  }
+  __syncthreads();
+
+  const long long nmt = (k.R + 15) / 16;
+  const long long nw = (long long)gridDim.x * 8;
+  // A inputs of m-tile mt: v[q] = V[16 mt + g8 + 8 (q & 1)][t4 + 4 (q >> 1)]
+  auto loadA = [&](long long mt, float2 (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long r = 16 * mt + g8 + 8 * (q & 1);
+      const int jt = t4 + 4 * (q >> 1);
+      v[q] = make_float2(0.f, 0.f);
+      if (r < k.R && jt < Jt) v[q] = __ldg(k.V + (size_t)r * Jt + jt);
+    }
+  };
+  // this warp's output tile [16 rows][LD]; columns past Nt are never copied out
+  const int LD = 8 * k.NTN + 4;
+  float* tile = reinterpret_cast<float*>(smem + sizeof(uint2) * (size_t)k.NTN * NP * 32) + warp * 16 * LD;
+  const bool out16 = ((reinterpret_cast<uintptr_t>(k.out) & 15u) == 0);
+  float2 vn[4];
+  long long mt = (long long)blockIdx.x * 8 + warp;
+  if (mt < nmt) loadA(mt, vn);
+  for (; mt < nmt; mt += nw) {
+    uint32_t ah[4], am[4], al[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = rnd<TF>(vn[q].x), y = rnd<TF>(vn[q].y);
+      if (SPLIT)
+        split3(x, y, ah[q], am[q], al[q]);
+      else
+        split2(x, y, ah[q], al[q]);
+    }
+    if (mt + nw < nmt) loadA(mt + nw, vn);
+    for (int nt = 0; nt < k.NTN; ++nt) {
+      const uint2* b = bfr + (size_t)nt * NP * 32 + lane;
+      const uint2 bh = b[0];
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      if (SPLIT) {
+        const uint2 bm = b[32], bl = b[64];
+        mma16(c, am[0], am[1], am[2], am[3], bm.x, bm.y);
+        mma16(c, al[0], al[1], al[2], al[3], bh.x, bh.y);
+        mma16(c, ah[0], ah[1], ah[2], ah[3], bl.x, bl.y);
+        mma16(c, am[0], am[1], am[2], am[3], bh.x, bh.y);
+        mma16(c, ah[0], ah[1], ah[2], ah[3], bm.x, bm.y);
+      }
+      mma16(c, ah[0], ah[1], ah[2], ah[3], bh.x, bh.y);
+      // c0, c1: row g8, t = 8 nt + 2 t4 (+1); c2, c3: row g8 + 8
+      const int t = 8 * nt + 2 * t4;
+      *reinterpret_cast<float2*>(tile + g8 * LD + t) = make_float2(c[0], c[1]);
+      *reinterpret_cast<float2*>(tile + (g8 + 8) * LD + t) = make_float2(c[2], c[3]);
+    }
+    __syncwarp();
+    // rows 16 mt .. 16 mt + nrow - 1 are out[16 mt Nt, (16 mt + nrow) Nt)
+    const long long rb = 16 * mt;
+    const int nrow = (int)min(16LL, k.R - rb);
+    const int cnt = nrow * Nt;
+    float* o = k.out + (size_t)rb * Nt;
+    auto at = [&](int e) -> float {
+      const int row = e / Nt;
+      return tile[row * LD + (e - row * Nt)];
+    };
+    if (out16 && (cnt & 3) == 0 && ((rb * Nt) & 3) == 0) {
+      float4* o4 = reinterpret_cast<float4*>(o);
+      for (int e4 = lane; e4 < cnt / 4; e4 += 32) {
+        float4 v = make_float4(at(4 * e4), at(4 * e4 + 1), at(4 * e4 + 2), at(4 * e4 + 3));
+        if (k.accumulate) {
+          const float4 c = o4[e4];
+          v.x += c.x;
+          v.y += c.y;
+          v.z += c.z;
+          v.w += c.w;
+        }
+        o4[e4] = v;
+      }
+    } else {
+      for (int e = lane; e < cnt; e += 32) o[e] = k.accumulate ? o[e] + at(e) : at(e);
+    }
+    __syncwarp();
+  }
+}
+
+bool synth_t_supported(int Nt, int Jt) { return Nt >= 1 && Nt <= 8 * kSynthNTMax && Jt >= 1 && Jt <= 8; }
+
+template <bool SPLIT, bool TF>
+static cudaError_t launch_synth_k(const SynthT& k, size_t smem, const char* name, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_synth_t<SPLIT, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_t<SPLIT, TF>, 256, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long tiles = (k.R + 15) / 16;
+  long long g = (long long)per_sm * sm_count();
+  if (g * 8 > tiles) g = (tiles + 7) / 8;
+  if (g < 1) g = 1;
+  FNO_LAUNCH(name, (k_synth_t<SPLIT, TF>), (int)g, 256, smem, s, k);
+  return cudaSuccess;
+}
+
+cudaError_t launch_synth_t(const float2* V, float* out, int64_t R, int Nt, int Jt, const float2* It,
+                           bool accumulate, bool split, bool tf32, cudaStream_t s) {
+  if (R <= 0) return cudaSuccess;
+  if (!synth_t_supported(Nt, Jt)) return cudaErrorInvalidValue;
+  SynthT k{};
+  k.V = V;
+  k.It = It;
+  k.out = out;
+  k.R = R;
+  k.Nt = Nt;
+  k.Jt = Jt;
+  k.NTN = (Nt + 7) / 8;
+  k.accumulate = accumulate ? 1 : 0;
+  split = split || tf32;
+  // basis fragments (at most 12 KB) and eight warp tiles of 16 x (8 NTN + 4) floats (at most 66 KB)
+  const size_t smem = sizeof(uint2) * (size_t)k.NTN * (split ? 3 : 1) * 32 +
+                      sizeof(float) * 8 * 16 * (size_t)(8 * k.NTN + 4);
+  if (tf32) return launch_synth_k<true, true>(k, smem, "fno_synth_t_tf32", s);
+  if (split) return launch_synth_k<true, false>(k, smem, "fno_synth_t_bf16x3", s);
+  return launch_synth_k<false, false>(k, smem, "fno_synth_t_bf16", s);
+}
+
 }  // namespace fno
 
 // ============================================================================

@@ -822,6 +822,115 @@ cudaError_t launch_pointwise_fwd(const float* x, const float* w, const float* bi
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// The block's 1x1 linear, bias and GELU for grids that the fused epilogues do
+// not tile, around the spectral part S synthesised into out:
+//   forward  A = out + bias + sum_i W(i, c) x[i];  out = GELU(A), gp = GELU'(A)
+//   dX       out = sum_i W(i, c) x[i]   (before S is added to out)
+// W(i, c) = w[i w_si + c w_sc].  A thread owns one point and holds all of its
+// outputs before it writes any, so x may be out itself (dA kept in dx).
+// FP32 on the CUDA cores, like the other pointwise layers.
+// ---------------------------------------------------------------------------
+struct PwAdd {
+  const float* x;
+  const float* w;
+  const float* bias;  // forward only (nullable)
+  float* out;
+  float* gp;          // forward, nullable
+  long long B, P;
+  int Cl, Cs, w_si, w_sc, fwd;
+};
+
+template <int CM>
+__global__ void __launch_bounds__(kPwThreads, 2) k_pw_add(const PwAdd k) {
+  extern __shared__ __align__(16) float sma[];
+  float* ws = sma;               // [Cl][CM], zero past Cs
+  float* bs = sma + k.Cl * CM;   // [CM]
+  for (int e = threadIdx.x; e < k.Cl * CM; e += blockDim.x) {
+    const int i = e / CM, c = e - i * CM;
+    ws[e] = (c < k.Cs) ? k.w[(long long)i * k.w_si + (long long)c * k.w_sc] : 0.f;
+  }
+  for (int c = threadIdx.x; c < CM; c += blockDim.x) bs[c] = (k.fwd && k.bias && c < k.Cs) ? k.bias[c] : 0.f;
+  __syncthreads();
+  const long long items = k.B * k.P;
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const long long b = it / k.P, p = it - b * k.P;
+    const float* xb = k.x + b * k.Cl * k.P + p;
+    float* ob = k.out + b * k.Cs * k.P + p;
+    // every load of the point first, so that they are all in flight at once
+    // (plain loads: x may alias out)
+    float acc[CM], xv[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) xv[i] = (i < k.Cl) ? xb[(long long)i * k.P] : 0.f;
+#pragma unroll
+    for (int c = 0; c < CM; ++c) acc[c] = bs[c] + ((k.fwd && c < k.Cs) ? ob[(long long)c * k.P] : 0.f);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (i >= k.Cl) break;
+      const float4* wr = reinterpret_cast<const float4*>(ws + i * CM);
+#pragma unroll
+      for (int c4 = 0; c4 < CM / 4; ++c4) {
+        const float4 wv = wr[c4];
+        acc[4 * c4 + 0] = fmaf(xv[i], wv.x, acc[4 * c4 + 0]);
+        acc[4 * c4 + 1] = fmaf(xv[i], wv.y, acc[4 * c4 + 1]);
+        acc[4 * c4 + 2] = fmaf(xv[i], wv.z, acc[4 * c4 + 2]);
+        acc[4 * c4 + 3] = fmaf(xv[i], wv.w, acc[4 * c4 + 3]);
+      }
+    }
+    float* gb = k.gp ? k.gp + b * k.Cs * k.P + p : nullptr;
+#pragma unroll
+    for (int c = 0; c < CM; ++c) {
+      if (c < k.Cs) {
+        const float a = acc[c];
+        if (k.fwd) {
+          float phi2, e;
+          phi2_as(a, phi2, e);
+          ob[(long long)c * k.P] = 0.5f * a * phi2;  // gelu_as(a)
+          if (gb) gb[(long long)c * k.P] = fmaf(a * e, 0.39894228040143268f, 0.5f * phi2);  // gelu_grad_as(a)
+        } else {
+          ob[(long long)c * k.P] = a;
+        }
+      }
+    }
+  }
+}
+
+bool pw_add_supported(int Cl, int Cs) { return Cl >= 1 && Cl <= 32 && Cs >= 1 && Cs <= 32; }
+
+template <int CM>
+static cudaError_t launch_pw_add_t(const PwAdd& a, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)a.Cl * CM + CM);
+  const long long items = a.B * a.P;
+  const long long cap = (long long)sm_count() * pw_blocks_per_sm((const void*)k_pw_add<CM>, smem);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(cap, (items + kPwThreads - 1) / kPwThreads));
+  FNO_LAUNCH(a.fwd ? "fno_pw_add_fwd" : "fno_pw_add_dx", k_pw_add<CM>, grid, kPwThreads, smem, s, a);
+  return cudaSuccess;
+}
+
+cudaError_t launch_pw_add(const float* x, const float* w, int w_si, int w_sc, const float* bias, float* out,
+                          float* gp, int64_t B, int64_t P, int Cl, int Cs, bool fwd, cudaStream_t s) {
+  if (B <= 0 || P <= 0) return cudaSuccess;
+  if (!pw_add_supported(Cl, Cs)) return cudaErrorInvalidValue;
+  PwAdd a{};
+  a.x = x;
+  a.w = w;
+  a.bias = bias;
+  a.out = out;
+  a.gp = gp;
+  a.B = B;
+  a.P = P;
+  a.Cl = Cl;
+  a.Cs = Cs;
+  a.w_si = w_si;
+  a.w_sc = w_sc;
+  a.fwd = fwd ? 1 : 0;
+  if (Cs <= 8) return launch_pw_add_t<8>(a, s);
+  if (Cs <= 16) return launch_pw_add_t<16>(a, s);
+  if (Cs <= 24) return launch_pw_add_t<24>(a, s);
+  return launch_pw_add_t<32>(a, s);
+}
+
 cudaError_t launch_pointwise_bwd(const float* x, const float* w, const float* bias,
                                  const float* dy, float* dx, float* part, int64_t B, int64_t P,
                                  int Ci, int Co, int act, int* rows_out, cudaStream_t s) {
