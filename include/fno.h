@@ -75,8 +75,14 @@ typedef struct fno_dims {
  * inverse z, t + epilogue stage runs, in FNO_BF16X3 and FNO_TF32, on tcgen05
  * (TMEM accumulators) for Nt = 16 or 32, Nz a multiple of 512 / Nt, 2 mz <= 24
  * and up to 32 channels; on warp-level mma.sync for FNO_BF16, the other shapes
- * its tiling takes and the dA pass of fno_block_bwd; and on the FP32 kernels
- * otherwise. */
+ * its tiling takes and the dA pass of fno_block_bwd.  Other Nt (the paper's 84
+ * and 86), with mt <= 8, up to 32 channels and the inverse z stage within the
+ * tensor-core line tiling, take a synthesis path: the inverse z stage and the
+ * inverse t stage to real points on mma.sync, the second written straight into
+ * the output, then the 1x1, bias and GELU in FP32 in place (a workspace region
+ * of B * max(C_in, C_out) * Nx * Ny * Nz * mt complex values holds the z stage;
+ * the recomputing backward's dA pass stays on the FP32 kernel).  The FP32
+ * kernels run the rest. */
 typedef enum fno_precision {
   FNO_FP32 = 0,
   FNO_TF32 = 1,
