@@ -157,3 +157,29 @@ def test_tc_unsupported_shapes_are_refused_not_run():
     with pytest.raises(_lib.FnoError) as ei:
         ops.spectral_fwd(x, w, (2, 2, 2, 9), "bf16x3")
     assert ei.value.status == -2
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16", "tf32"])
+def test_paper_nt_runs_the_tensor_core_synthesis_path(precision):
+    # Nt = 86 (the CO2 data's t axis) is outside the fused epilogues' tiling:
+    # the forward and dX epilogues take the inverse-t synthesis kernel and the
+    # in-place pointwise pass, and still match the oracle
+    from paper_2211_12709_gb300 import _lib, ops
+    d = Dims(1, 3, 4, 4, 3, 20, 86, 1, 1, 4, 8)
+    x, w, wl, b, dz = make_case(d, 13)
+    X, W, WL, Bb, DZ = gpu(x), gpu(w), gpu(wl), gpu(b), gpu(dz)
+    torch.cuda.synchronize()
+    _lib.fno_profile_start()
+    z = ops.block_fwd(X, W, WL, Bb, modes_of(d), precision)
+    dx, dw, dwl, db = ops.block_bwd(X, W, WL, Bb, DZ, modes_of(d), precision)
+    torch.cuda.synchronize()
+    prof = _lib.fno_profile_stop()
+    names = set(prof)
+    assert f"fno_synth_t_{precision}" in names, names
+    assert "fno_pw_add_fwd" in names and "fno_pw_add_dx" in names, names
+    rz, _ = oracle.block_fwd(d, x, w, wl, b)
+    rg = oracle.block_bwd(d, x, w, dz, wl, b)
+    errs = {"z": relerr(host(z), rz), "dx": relerr(host(dx), rg["dx"]),
+            "dw": relerr(host(dw), rg["dw"]), "dwl": relerr(host(dwl), rg["dwl"]),
+            "db": relerr(host(db), rg["db"])}
+    assert all(v <= TOL[precision] for v in errs.values()), errs
