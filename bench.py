@@ -161,6 +161,16 @@ def algorithmic(name, d):
         return 3 * grid + t1, f_inv + 2 * f_lin
     if name.startswith("fno_epi_dx"):
         return 2 * grid + t1, f_inv + f_lin
+    # the synthesis path (grids the fused epilogues do not tile, e.g. Nt = 84, 86)
+    if name.startswith("fno_synth_t"):
+        # inverse t to real points: reads V = [B C Nx Ny][Nz][Jt]; the forward
+        # writes the output, the dX form reads and writes it (one launch of
+        # each per step, so a launch averages 1.5 output tensors)
+        return 8 * ncolz * Nz * Jt + 3 * grid // 2, ncolz * Nz * Nt * Jt * 4
+    if name.startswith("fno_pw_add_fwd"):  # training forward: reads x and S, writes z and GELU'(A)
+        return 4 * grid, f_lin
+    if name.startswith("fno_pw_add_dx"):  # reads dA, writes W dA
+        return 2 * grid, f_lin
     Mk = Jx * Jy * Jz * Jt
     nchunk = (B + 7) // 8  # batch chunks of the mixing kernels (W crosses HBM once per chunk)
     if name.startswith("fno_mix_adjoint"):
@@ -202,7 +212,7 @@ def roofline_of(name, per_launch_ms, dd, pk, precision):
     gbs = nbytes / sec / 1e9
     tfl = nflops / sec / 1e12
     f_hbm = gbs / pk["hbm_gbs"]
-    if "_tc_" in name or "_mma_" in name or name.startswith("fno_da_tz"):
+    if "_tc_" in name or "_mma_" in name or name.startswith(("fno_da_tz", "fno_synth_t")):
         # tensor-core kernels (mma.sync): algorithmic flops against
         # the dense BF16 peak; split BF16 issues 3 (DFT stages) or 6 (1x1
         # stages) products per real multiply-add, which the fraction leaves out

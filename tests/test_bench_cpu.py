@@ -46,8 +46,8 @@ def test_every_heavy_launch_has_algorithmic_bytes():
     b = _bench()
     heavy = [n for n in launch_names()
              if n.startswith(("fno_epi_fwd", "fno_epi_da", "fno_epi_dx", "fno_fwd_tz", "fno_da_saved",
-                              "fno_da_tz", "fno_mix"))]
-    assert len(heavy) >= 20
+                              "fno_da_tz", "fno_mix", "fno_synth_t", "fno_pw_add"))]
+    assert len(heavy) >= 25
     for n in heavy:
         nbytes, _ = b.algorithmic(n, DD)
         # every one moves at least one activation tensor, except the mixing
@@ -79,3 +79,21 @@ def test_roofline_fraction_is_algorithmic_bytes_over_time_over_peak():
     assert abs(r["achieved"] - achieved) < 0.5
     assert abs(r["frac"] - achieved / 6754.1) < 1e-3
     assert r["traffic"] is not None and abs(r["traffic"] / nbytes - 1) < 0.05
+
+
+def test_synthesis_path_counts_its_tensors():
+    # at the CO2 paper grid (B 1, width 20, 262 x 118 x 64 x 86, modes 26/12/6/8)
+    b = _bench()
+    dd = {"B": 1, "Ci": 20, "Co": 20, "Nx": 262, "Ny": 118, "Nz": 64, "Nt": 86,
+          "Jx": 52, "Jy": 24, "Jz": 12, "Jt": 8}
+    grid = 4 * 20 * 262 * 118 * 64 * 86
+    v = 8 * 20 * 262 * 118 * 64 * 8  # the inverse z stage's output, complex64
+    assert b.algorithmic("fno_pw_add_fwd", dd)[0] == 4 * grid
+    assert b.algorithmic("fno_pw_add_dx", dd)[0] == 2 * grid
+    sb, sf = b.algorithmic("fno_synth_t_bf16x3", dd)
+    assert sb == v + 3 * grid // 2
+    assert sf == 20 * 262 * 118 * 64 * 86 * 8 * 4  # (re, im) products per point, mode and channel
+    pk = {"hbm_gbs": 6685.5, "bf16_tflops": 1942.4, "sm_max_mhz": 2070.0, "src": "measured"}
+    assert b.roofline_of("fno_synth_t_bf16x3", 5.148, dd, pk, "bf16x3")["bound"] == "hbm"
+    r = b.roofline_of("fno_pw_add_fwd", 13.985, dd, pk, "bf16x3")
+    assert r["bound"] == "hbm" and abs(r["frac"] - 4 * grid / 13.985e-3 / 1e9 / 6685.5) < 1e-3
