@@ -181,3 +181,15 @@ def test_adam_arguments_are_checked_on_the_host():
     assert lib.fno_adam_step(16, *ok, -1.0, 0.9, 0.999, 1e-8, 1, None) == -1   # lr < 0
     assert lib.fno_adam_step(16, None, 256, 256, 256, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
     assert lib.fno_adam_step(0, None, None, None, None, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0
+
+
+def test_workspace_holds_the_synthesis_region_only_outside_the_fused_tiling():
+    # Nt = 32 is tiled by the fused epilogues; Nt = 30 takes the synthesis path,
+    # whose inverse z stage needs B * C * Nx * Ny * Nz * mt complex64 values
+    def ws(nt):
+        d = _lib.make_dims(1, 8, 8, 16, 16, 32, nt, 4, 4, 4, 8)
+        return _lib.fno_workspace_bytes(d, _lib.FNO_BF16X3, _lib.FNO_OP_SPECTRAL_FWD)
+    v = 8 * 1 * 8 * 16 * 16 * 32 * 8
+    diff = ws(30) - ws(32)
+    # the t tables (Jt x Nt) and the fused epilogues' basis tables differ by a few KB
+    assert abs(diff - v) < (1 << 20), (diff, v)
