@@ -345,8 +345,9 @@ static cudaError_t synth_epilogue(const Dims& d, const EpiArgs& a, int precision
 
 // The fused inverse z, t + epilogue stage: split BF16 and TF32 on tcgen05 (TMEM
 // accumulators) where its tiling applies, then warp-level mma.sync (plain BF16,
-// the dA mode and the shapes tcgen05 does not tile), else FP32 on the CUDA
-// cores (the plain form, and the exact fallback for other shapes).
+// the dA mode and the shapes tcgen05 does not tile), then, in the tensor-core
+// precisions, the synthesis path for other Nt (not the dA mode), else FP32 on
+// the CUDA cores (the plain form, and the exact fallback for other shapes).
 static cudaError_t epilogue(const Dims& d, EpiArgs a, int precision, char* base, const Layout& L,
                             int* err, int* grid_used, cudaStream_t s) {
   // plain BF16 (one product, no split operands to build) measured faster on
